@@ -1,0 +1,172 @@
+/*
+ * pspec.h — C ABI of libpspec, the GB300 (sm_103a) implementation of the
+ * spherical-harmonic FFT estimator of power-spectrum multipoles P_l(k) with a
+ * moving (local plane-parallel) line of sight, and of the P(k, mu) wedges built
+ * from them (Hand, Li, Slepian & Seljak 2017, arXiv:1704.02357).
+ *
+ * Operations and where the paper defines them
+ *   pspec_paint       Sec. 2.1 eq. FKP-density (F = w [n - alpha n_s], I, alpha) and
+ *                     the shot-noise term after eq. Pell-full; Sec. 2.3 mass assignment
+ *                     (CIC / TSC) and the interlaced second mesh.
+ *   pspec_multipoles  Sec. 2.1 eqs. Pell-ours and Fell with the real harmonics of
+ *                     eq. real-Ylm (2l+1 real-to-complex transforms per multipole);
+ *                     Sec. 2.3 interlacing, window compensation and the inverse
+ *                     transform before the Y_lm weighting; k-shell averages.
+ *   pspec_wedges      Sec. 2.2 eqs. wedge-est and Lbar.
+ *
+ * Conventions (shared by every entry point)
+ *   - Mesh: N^3 nodes at corner + i*H, H = box_size/N, index order (x, y, z), z fastest.
+ *   - Forward transforms use exp(-i k.x); integer frequencies n in [-N/2, N/2).
+ *   - alpha = sum of data completeness weights / sum of randoms completeness weights;
+ *     I = alpha * sum_randoms nbar w_c w_fkp^2; S = sum_data v^2 + alpha^2 sum_randoms v^2,
+ *     v = w_c * w_fkp, w_fkp = 1/(1 + nbar P0) (1 when P0 = 0). S is subtracted from
+ *     l = 0 only.
+ *   - When interlacing or compensation is on, modes with some n_d = -N/2 are zeroed
+ *     before the inverse transform. Modes with some n_d = -N/2, and k = 0, are never
+ *     binned. Mode n lies in bin b iff t_b <= |n|^2 < t_{b+1}, t_b = (k_b L / 2pi)^2 (FP64).
+ *
+ * Ownership and errors
+ *   - Every call returns a pspec_status. No exception crosses the ABI. pspec_strerror()
+ *     names a status; pspec_last_error() gives the detail of the last failure on a context.
+ *   - The caller owns every pointer it passes. Device memory for meshes, spectra and
+ *     tables is one caller-provided workspace (size from pspec_workspace_size) that must
+ *     stay allocated until pspec_destroy; the library allocates no device memory itself.
+ *   - All device work is enqueued on the stream given to pspec_create, in call order.
+ *     Calls on one context are not thread-safe; distinct contexts are independent.
+ *   - Host output pointers are written before the call returns (the call synchronises
+ *     the stream). The *_device variants write device buffers and return without
+ *     synchronising.
+ *   - Invalid arguments give PSPEC_EINVAL and leave the context usable. A CUDA error
+ *     gives PSPEC_ECUDA; the context should then be destroyed.
+ */
+#ifndef PSPEC_H
+#define PSPEC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t pspec_status;
+enum {
+  PSPEC_OK = 0,
+  PSPEC_EINVAL = 1,        /* bad argument: sizes, edges, l, pointers, non-finite inputs */
+  PSPEC_ENOMEM = 2,        /* workspace too small */
+  PSPEC_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+  PSPEC_ETIMEOUT = 4,      /* a bounded device-side wait ran out */
+  PSPEC_ECANCELED = 5,     /* the caller cancelled the work */
+  PSPEC_EUNSUPPORTED = 6,  /* valid but not implemented here: odd l, l > 16, N not 2^a or 3*2^a */
+  PSPEC_ESTATE = 7         /* call out of order (e.g. multipoles before paint) */
+};
+
+enum { PSPEC_WINDOW_CIC = 2, PSPEC_WINDOW_TSC = 3 };   /* value = order p of sinc^p */
+enum { PSPEC_FP32 = 0, PSPEC_FP64 = 1 };
+enum { PSPEC_POS_F64 = 0, PSPEC_POS_F32 = 1 };
+#define PSPEC_MAX_ELL 16
+#define PSPEC_MAX_KBINS 4096
+#define PSPEC_MAX_MU 64
+
+typedef struct {
+  int32_t nmesh;           /* N: even, 8 <= N <= 1024, N = 2^a or 3*2^a */
+  int32_t window;          /* PSPEC_WINDOW_CIC or PSPEC_WINDOW_TSC */
+  int32_t interlaced;      /* 0/1: paint a second mesh shifted by H/2 (Sec. 2.3) */
+  int32_t compensate;      /* 0/1: divide by prod_d sinc^p(pi n_d/N) */
+  int32_t precision;       /* PSPEC_FP32 (FP32 meshes/transforms, FP64 sums and bins) or PSPEC_FP64 */
+  int32_t ell_max;         /* largest even l this context will be asked for, <= 16 */
+  double box_size;         /* L */
+  double box_corner[3];    /* position of node (0,0,0) */
+  double observer[3];      /* origin of the line of sight */
+  double P0;               /* FKP P0; 0 gives w_fkp = 1 */
+  double nbar;             /* n̄ used for particles whose catalog has no nbar array */
+  int64_t max_group_bytes; /* cap on the per-group spectrum buffers; 0 = one whole multipole */
+} pspec_params;
+
+typedef struct {
+  const void* pos;         /* device, count x 3 row-major, dtype per pos_dtype */
+  int32_t pos_dtype;       /* PSPEC_POS_F64 or PSPEC_POS_F32 */
+  const double* weight;    /* device, completeness weight w_c per particle, or NULL (= 1) */
+  const double* nbar;      /* device, n̄ per particle, or NULL (= params.nbar) */
+  int64_t count;           /* number of particles, >= 0 (randoms need > 0) */
+} pspec_catalog;
+
+typedef struct {
+  double alpha, I, S;      /* as defined above */
+  double W_d, W_r;         /* sums of completeness weights */
+  int64_t n_nonfinite;     /* particles with a non-finite weight or nbar, or a position non-finite or
+                              more than 2^40 cells from the corner (an error) */
+  int64_t n_wrapped;       /* particles outside [corner, corner + L)^3, painted periodically */
+} pspec_stats;
+
+/* Device bytes a context with these parameters needs for a multipole call with up to
+ * `max_kbins` bins. Returns PSPEC_EINVAL / PSPEC_EUNSUPPORTED for bad parameters. */
+pspec_status pspec_workspace_size(const pspec_params* p, int32_t max_kbins, int64_t* bytes);
+
+/* Create a context on CUDA device `device`, enqueuing on `stream` (a cudaStream_t, or NULL
+ * for the legacy default stream). `workspace` is a device buffer of at least
+ * pspec_workspace_size() bytes, 256-byte aligned, owned by the caller. */
+pspec_status pspec_create(const pspec_params* p, int32_t device, void* stream, void* workspace,
+                          int64_t workspace_bytes, int32_t max_kbins, void** ctx);
+pspec_status pspec_destroy(void* ctx);
+
+/* Step a1 + a2: FP64 catalog sums (alpha, I, S) and painting of data (+v) and randoms
+ * (-alpha v) onto the mesh(es). Positions, weights and nbar are read on the device.
+ * `stats` (host, nullable) is filled after a stream synchronisation, and an invalid
+ * particle (see n_nonfinite) then gives PSPEC_EINVAL. With stats == NULL the call does not
+ * synchronise and invalid particles are left out of the sums and the meshes. */
+pspec_status pspec_paint(void* ctx, const pspec_catalog* data, const pspec_catalog* randoms,
+                         pspec_stats* stats);
+
+/* Steps a3-a6 on the painted meshes: P[i*n_kbins + b] for l = ells[i], k_mean[b] and
+ * n_modes[b], all host arrays. `ells` (host) are even, <= the context's ell_max, any order,
+ * no repeats. `k_edges` (host) has n_kbins + 1 strictly increasing, finite, >= 0 values.
+ * Empty bins give NaN in P and k_mean and 0 in n_modes. */
+pspec_status pspec_multipoles(void* ctx, const int32_t* ells, int32_t n_ells,
+                              const double* k_edges, int32_t n_kbins,
+                              double* P, double* k_mean, double* n_modes);
+
+/* As pspec_multipoles, but P, k_mean and n_modes are device buffers and the call does not
+ * synchronise (capturable in a CUDA graph once the same ells/k_edges were seen before). */
+pspec_status pspec_multipoles_device(void* ctx, const int32_t* ells, int32_t n_ells,
+                                     const double* k_edges, int32_t n_kbins,
+                                     double* P_dev, double* k_mean_dev, double* n_modes_dev);
+
+/* Step a7: out[w*n_kbins + b] = sum_i P[i*n_kbins + b] * Lbar_{ells[i]}(mu_w, mu_{w+1}).
+ * P and out are DEVICE arrays; ells and mu_edges are host arrays; the mean Legendre
+ * table is built in FP64 on the host. mu_edges: n_mu + 1 increasing values in [0, 1].
+ * Enqueued on `stream` without synchronising. */
+pspec_status pspec_wedges(const double* P, const int32_t* ells, int32_t n_ells, int32_t n_kbins,
+                          const double* mu_edges, int32_t n_mu, double* out, void* stream);
+
+/* Plan facts for tests and reports. */
+typedef struct {
+  int32_t nmesh, precision, ell_max;
+  int32_t tile_y, tile_x, tile_bin, rows_z;   /* FFT tile shapes chosen */
+  int32_t group_max;                          /* spectra buffered per group launch */
+  int32_t bin_ctas;                           /* persistent CTAs of the binning passes */
+  int64_t sh_transforms;                      /* sum over requested l of 2l+1 (paper's count) */
+  int64_t transforms_executed;                /* 3-D transforms of the last multipoles call */
+  int64_t kernel_launches;                    /* cumulative kernels launched by this context */
+  double model_bytes_last;                    /* algorithmic HBM bytes of the last paint+multipoles */
+} pspec_plan_info;
+pspec_status pspec_get_plan_info(void* ctx, pspec_plan_info* info);
+
+/* Per-kernel-class timing with CUDA events on the context's stream, for the benchmark.
+ * While enabled, each launch is bracketed by events; pspec_kernel_times returns, per
+ * class, the number of launches, the summed milliseconds and the algorithmic bytes. */
+enum { PSPEC_K_SUMS = 0, PSPEC_K_PAINT, PSPEC_K_FFT_Z, PSPEC_K_FFT_Y, PSPEC_K_FFT_X,
+       PSPEC_K_COMBINE, PSPEC_K_YLM_Z, PSPEC_K_BIN_X, PSPEC_K_C2R_Z, PSPEC_K_FINAL,
+       PSPEC_K_OTHER, PSPEC_K_COUNT };
+pspec_status pspec_set_profiling(void* ctx, int32_t enable);
+pspec_status pspec_kernel_times(void* ctx, int64_t* launches, double* ms, double* bytes);
+const char* pspec_kernel_name(int32_t k);
+
+const char* pspec_strerror(pspec_status s);
+const char* pspec_last_error(void* ctx);
+/* Library version string and the compiled-in architecture. */
+const char* pspec_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSPEC_H */

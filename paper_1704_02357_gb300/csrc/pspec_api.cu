@@ -1,0 +1,729 @@
+// C ABI of libpspec: plan, workspace layout, argument validation and the launch sequence
+// of the SH-FFT multipole estimator (declarations and conventions in include/pspec.h).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+#include <algorithm>
+#include "pspec.h"
+#include "launch.h"
+
+using namespace pspec;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr size_t kSmemBudget = 200 * 1024;
+constexpr int kMaxElls = PSPEC_MAX_ELL / 2 + 1;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+bool good_nmesh(int n) {
+  if (n < 8 || n > 1024 || (n & 1)) return false;
+  int x = n;
+  while ((x & 1) == 0) x >>= 1;
+  return x == 1 || x == 3;
+}
+
+FftPlan make_fft(int L) {
+  FftPlan p{};
+  p.L = L;
+  int x = L, ns = 1;
+  auto push = [&](int r) {
+    p.rad[p.nst] = r;
+    p.ns[p.nst] = ns;
+    ns *= r;
+    p.nst++;
+    x /= r;
+  };
+  while (x % 3 == 0) push(3);
+  while (x % 8 == 0) push(8);
+  while (x % 4 == 0) push(4);
+  while (x % 2 == 0) push(2);
+  return p;
+}
+
+int pow2_floor(int v) {
+  int p = 1;
+  while (p * 2 <= v) p *= 2;
+  return p;
+}
+
+struct Plan {
+  Geo g;
+  int esz;          // sizeof(T)
+  FftPlan pz, pf;
+  int tw_y, tw_x, tw_comb, tw_bin, rows_z;
+  int group_max;
+  int ctas_comb, ctas_bin, ctas_max;
+  int nblk_sum;
+  int nslots_max;
+  bool roundtrip;
+  size_t Sr, Sc;
+  // workspace offsets
+  size_t o_mesh1, o_mesh2, o_f0, o_w, o_f, o_g, o_twh, o_twf, o_twr, o_axis, o_phase, o_invw, o_bin,
+      o_kmag, o_sums, o_derived, o_part, o_out, total;
+  int n2max;
+};
+
+template <typename T> size_t cx_size() { return sizeof(cx<T>); }
+
+int pick_tw(int NH, size_t per_tw_bytes, size_t fixed, size_t budget, int max_tw) {
+  for (int tw = max_tw; tw >= 1; tw >>= 1)
+    if (NH % tw == 0 && fixed + per_tw_bytes * (size_t)tw <= budget) return tw;
+  return 1;
+}
+
+pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl, std::string* why) {
+  if (!p) { *why = "params is NULL"; return PSPEC_EINVAL; }
+  if (!good_nmesh(p->nmesh)) { *why = "nmesh must be even, 8..1024, 2^a or 3*2^a"; return PSPEC_EUNSUPPORTED; }
+  if (p->window != PSPEC_WINDOW_CIC && p->window != PSPEC_WINDOW_TSC) { *why = "window must be CIC or TSC"; return PSPEC_EINVAL; }
+  if (p->precision != PSPEC_FP32 && p->precision != PSPEC_FP64) { *why = "precision must be FP32 or FP64"; return PSPEC_EINVAL; }
+  if (p->ell_max < 0 || (p->ell_max & 1)) { *why = "ell_max must be even and >= 0"; return PSPEC_EUNSUPPORTED; }
+  if (p->ell_max > PSPEC_MAX_ELL) { *why = "ell_max > 16"; return PSPEC_EUNSUPPORTED; }
+  if (!(std::isfinite(p->box_size) && p->box_size > 0)) { *why = "box_size must be finite and > 0"; return PSPEC_EINVAL; }
+  for (int d = 0; d < 3; d++)
+    if (!std::isfinite(p->box_corner[d]) || !std::isfinite(p->observer[d])) { *why = "corner/observer must be finite"; return PSPEC_EINVAL; }
+  if (!(std::isfinite(p->P0) && p->P0 >= 0) || !(std::isfinite(p->nbar) && p->nbar >= 0)) { *why = "P0 and nbar must be finite and >= 0"; return PSPEC_EINVAL; }
+  if (max_kbins < 1 || max_kbins > PSPEC_MAX_KBINS) { *why = "max_kbins out of range"; return PSPEC_EINVAL; }
+  if (p->max_group_bytes < 0) { *why = "max_group_bytes < 0"; return PSPEC_EINVAL; }
+
+  const bool f64 = p->precision == PSPEC_FP64;
+  const int N = p->nmesh, NH = N / 2;
+  pl->g.N = N;
+  pl->g.NH = NH;
+  pl->esz = f64 ? 8 : 4;
+  const size_t csz = f64 ? 16 : 8;
+  pl->pz = make_fft(NH);
+  pl->pf = make_fft(N);
+  pl->roundtrip = p->interlaced || p->compensate;
+  pl->Sr = (size_t)N * N * N * pl->esz;
+  pl->Sc = (size_t)N * N * NH * csz;
+
+  const size_t budget2 = 110 * 1024;   // two CTAs per SM
+  pl->tw_y = pick_tw(NH, 2 * N * csz, N * csz, budget2, 16);
+  pl->tw_x = pl->tw_y;
+  pl->tw_comb = pick_tw(NH, 2 * N * csz, N * csz + 3 * (size_t)max_kbins * 8, budget2, 16);
+  pl->tw_bin = pick_tw(NH, 3 * N * csz + N * pl->esz, N * csz + (size_t)max_kbins * 8, budget2, 8);
+  if (pl->tw_bin < 1) pl->tw_bin = 1;
+  pl->rows_z = std::max(1, pow2_floor(std::max(1, 2048 / NH)));
+  while ((int64_t)N * N % pl->rows_z) pl->rows_z >>= 1;
+
+  const int nharm = 2 * p->ell_max + 1;
+  int m_smem = (int)((kSmemBudget / csz - 2 * (size_t)NH) / (2 * (size_t)NH));
+  int m_mem = p->max_group_bytes > 0 ? (int)(p->max_group_bytes / (int64_t)pl->Sc) : nharm;
+  pl->group_max = std::max(1, std::min(nharm, std::min(m_smem, m_mem)));
+  if (p->ell_max == 0) pl->group_max = 0;
+
+  if (f64) {
+    pl->ctas_comb = combine_x_ctas<double>(pl->g, pl->tw_comb, nsm, max_kbins);
+    pl->ctas_bin = bin_x_ctas<double>(pl->g, pl->tw_bin, nsm, max_kbins);
+  } else {
+    pl->ctas_comb = combine_x_ctas<float>(pl->g, pl->tw_comb, nsm, max_kbins);
+    pl->ctas_bin = bin_x_ctas<float>(pl->g, pl->tw_bin, nsm, max_kbins);
+  }
+  pl->ctas_max = std::max(pl->ctas_comb, pl->ctas_bin);
+  pl->nblk_sum = 2 * nsm;
+  pl->nslots_max = SLOT_ELL0 + kMaxElls;
+  pl->n2max = 3 * NH * NH;
+
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes); return at; };
+  pl->o_mesh1 = take(pl->Sr);
+  pl->o_mesh2 = p->interlaced ? take(pl->Sr) : 0;
+  pl->o_f0 = take(pl->Sc);
+  pl->o_w = take(pl->Sc);
+  pl->o_f = pl->roundtrip ? take(pl->Sr) : 0;
+  pl->o_g = pl->group_max ? take(pl->Sc * pl->group_max) : 0;
+  pl->o_twh = take(NH * csz);
+  pl->o_twf = take(N * csz);
+  pl->o_twr = take(NH * csz);
+  pl->o_axis = take(3 * (size_t)N * pl->esz);
+  pl->o_phase = take((N + NH) * csz);
+  pl->o_invw = take((N + NH) * (size_t)pl->esz);
+  pl->o_bin = take((pl->n2max + 1) * sizeof(int32_t));
+  pl->o_kmag = take((pl->n2max + 1) * sizeof(double));
+  pl->o_sums = take(2 * (size_t)pl->nblk_sum * kSumVals * sizeof(double));
+  pl->o_derived = take(D_COUNT * sizeof(double));
+  pl->o_part = take((size_t)pl->ctas_max * pl->nslots_max * max_kbins * sizeof(double));
+  pl->o_out = take(((size_t)kMaxElls + 2) * max_kbins * sizeof(double));
+  pl->total = o;
+  return PSPEC_OK;
+}
+
+struct Ctx {
+  pspec_params p;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  char* ws = nullptr;
+  int64_t ws_bytes = 0;
+  int max_kbins = 0;
+  int nsm = 0;
+  Plan pl;
+  bool painted = false;
+  std::vector<double> edges;
+  std::string err;
+  int64_t launches = 0;
+  int64_t transforms_last = 0;
+  int64_t sh_last = 0;
+  double bytes_paint = 0, bytes_mult = 0;
+  // profiling
+  bool prof = false;
+  struct Rec { int k; cudaEvent_t a, b; double bytes; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  int64_t k_launch[PSPEC_K_COUNT] = {};
+  double k_ms[PSPEC_K_COUNT] = {};
+  double k_bytes[PSPEC_K_COUNT] = {};
+
+  template <typename U> U* at(size_t off) { return reinterpret_cast<U*>(ws + off); }
+};
+
+cudaEvent_t take_event(Ctx* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Launch wrapper: counts launches, brackets with events when profiling, checks errors.
+template <typename F>
+pspec_status run(Ctx* c, int kclass, double bytes, F&& launch) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (c->prof) {
+    a = take_event(c);
+    b = take_event(c);
+    cudaEventRecord(a, c->stream);
+  }
+  launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    c->err = std::string("kernel launch failed: ") + cudaGetErrorString(e);
+    return PSPEC_ECUDA;
+  }
+  c->launches++;
+  if (c->prof) {
+    cudaEventRecord(b, c->stream);
+    c->recs.push_back({kclass, a, b, bytes});
+  }
+  return PSPEC_OK;
+}
+
+#define TRY(x)                       \
+  do {                               \
+    pspec_status _s = (x);           \
+    if (_s != PSPEC_OK) return _s;   \
+  } while (0)
+
+pspec_status cuda_fail(Ctx* c, cudaError_t e, const char* what) {
+  c->err = std::string(what) + ": " + cudaGetErrorString(e);
+  return PSPEC_ECUDA;
+}
+
+template <typename T>
+pspec_status upload_tables(Ctx* c) {
+  const Plan& pl = c->pl;
+  const int N = pl.g.N, NH = pl.g.NH;
+  using C = cx<T>;
+  std::vector<C> twh(NH), twf(N), twr(NH), phase(N + NH);
+  std::vector<T> axis(3 * N), invw(N + NH);
+  for (int t = 0; t < NH; t++) {
+    const double a = -2.0 * M_PI * t / NH;
+    twh[t] = mk(T(std::cos(a)), T(std::sin(a)));
+    const double b = -2.0 * M_PI * t / N;
+    twr[t] = mk(T(std::cos(b)), T(std::sin(b)));
+  }
+  for (int t = 0; t < N; t++) {
+    const double a = -2.0 * M_PI * t / N;
+    twf[t] = mk(T(std::cos(a)), T(std::sin(a)));
+  }
+  const double H = c->p.box_size / N;
+  for (int d = 0; d < 3; d++)
+    for (int i = 0; i < N; i++) axis[d * N + i] = T(c->p.box_corner[d] + i * H - c->p.observer[d]);
+  const int p = c->p.window;  // sinc order
+  auto sincp = [&](int n) {
+    if (n == 0) return 1.0;
+    const double x = M_PI * n / N;
+    return std::pow(std::sin(x) / x, p);
+  };
+  for (int i = 0; i < N + NH; i++) {
+    const int n = i < N ? (i < NH ? i : i - N) : (i - N);
+    const double a = -M_PI * n / N;  // exp(-i pi n / N): the H/2 shift of the second mesh
+    phase[i] = mk(T(std::cos(a)), T(std::sin(a)));
+    invw[i] = T(1.0 / sincp(n));
+  }
+  cudaError_t e;
+  e = cudaMemcpyAsync(c->at<C>(pl.o_twh), twh.data(), NH * sizeof(C), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->at<C>(pl.o_twf), twf.data(), N * sizeof(C), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->at<C>(pl.o_twr), twr.data(), NH * sizeof(C), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->at<T>(pl.o_axis), axis.data(), 3 * N * sizeof(T), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->at<C>(pl.o_phase), phase.data(), (N + NH) * sizeof(C), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->at<T>(pl.o_invw), invw.data(), (N + NH) * sizeof(T), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "table upload");
+  return PSPEC_OK;
+}
+
+// Bin decision of every |n|^2 in FP64: b iff t_b <= n2 < t_{b+1}, t_b = (k_b L/(2 pi))^2.
+pspec_status upload_bins(Ctx* c, const double* edges, int nk) {
+  std::vector<double> e(edges, edges + nk + 1);
+  if (e == c->edges) return PSPEC_OK;
+  const Plan& pl = c->pl;
+  std::vector<double> t(nk + 1);
+  for (int b = 0; b <= nk; b++) {
+    const double x = e[b] * c->p.box_size / (2.0 * M_PI);
+    t[b] = x * x;
+  }
+  std::vector<int32_t> bin(pl.n2max + 1);
+  std::vector<double> kmag(pl.n2max + 1);
+  const double kf = 2.0 * M_PI / c->p.box_size;
+  for (int n2 = 0; n2 <= pl.n2max; n2++) {
+    const double x = (double)n2;
+    int b = -1;
+    if (n2 > 0 && x >= t[0] && x < t[nk]) {
+      b = (int)(std::upper_bound(t.begin(), t.end(), x) - t.begin()) - 1;
+    }
+    bin[n2] = b;
+    kmag[n2] = kf * std::sqrt(x);
+  }
+  cudaError_t er = cudaMemcpyAsync(c->at<int32_t>(pl.o_bin), bin.data(), bin.size() * sizeof(int32_t),
+                                   cudaMemcpyHostToDevice, c->stream);
+  if (er == cudaSuccess)
+    er = cudaMemcpyAsync(c->at<double>(pl.o_kmag), kmag.data(), kmag.size() * sizeof(double),
+                         cudaMemcpyHostToDevice, c->stream);
+  if (er == cudaSuccess) er = cudaStreamSynchronize(c->stream);
+  if (er != cudaSuccess) return cuda_fail(c, er, "bin table upload");
+  c->edges = e;
+  return PSPEC_OK;
+}
+
+pspec_status check_catalog(Ctx* c, const pspec_catalog* cat, const char* name, bool need_points) {
+  if (!cat) { c->err = std::string(name) + " catalog is NULL"; return PSPEC_EINVAL; }
+  if (cat->count < 0) { c->err = std::string(name) + " count < 0"; return PSPEC_EINVAL; }
+  if (need_points && cat->count == 0) { c->err = std::string(name) + " catalog is empty"; return PSPEC_EINVAL; }
+  if (cat->count > 0 && !cat->pos) { c->err = std::string(name) + " positions are NULL"; return PSPEC_EINVAL; }
+  if (cat->pos_dtype != PSPEC_POS_F64 && cat->pos_dtype != PSPEC_POS_F32) { c->err = "pos_dtype"; return PSPEC_EINVAL; }
+  return PSPEC_OK;
+}
+
+PaintArgs paint_args(Ctx* c, const pspec_catalog* cat) {
+  PaintArgs a;
+  a.pos = cat->pos;
+  a.pos_f32 = cat->pos_dtype == PSPEC_POS_F32;
+  a.weight = cat->weight;
+  a.nbar = cat->nbar;
+  a.count = cat->count;
+  for (int d = 0; d < 3; d++) a.corner[d] = c->p.box_corner[d];
+  a.cell = c->p.box_size / c->p.nmesh;
+  a.P0 = c->p.P0;
+  a.nbar_default = c->p.nbar;
+  return a;
+}
+
+double cat_bytes(const pspec_catalog* cat) {
+  const double per = (cat->pos_dtype == PSPEC_POS_F32 ? 12.0 : 24.0) + (cat->weight ? 8.0 : 0.0) +
+                     (cat->nbar ? 8.0 : 0.0);
+  return per * (double)cat->count;
+}
+
+template <typename T>
+pspec_status do_paint(Ctx* c, const pspec_catalog* d, const pspec_catalog* r) {
+  const Plan& pl = c->pl;
+  const int N = pl.g.N;
+  T* m1 = c->at<T>(pl.o_mesh1);
+  T* m2 = c->p.interlaced ? c->at<T>(pl.o_mesh2) : nullptr;
+  cudaError_t e = cudaMemsetAsync(m1, 0, pl.Sr, c->stream);
+  if (e == cudaSuccess && m2) e = cudaMemsetAsync(m2, 0, pl.Sr, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "mesh clear");
+  double* sums = c->at<double>(pl.o_sums);
+  double* part_d = sums;
+  double* part_r = sums + (size_t)pl.nblk_sum * kSumVals;
+  double* der = c->at<double>(pl.o_derived);
+  const PaintArgs ad = paint_args(c, d), ar = paint_args(c, r);
+  TRY(run(c, PSPEC_K_SUMS, cat_bytes(d), [&] { launch_catalog_partials(ad, N, part_d, pl.nblk_sum, c->stream); }));
+  TRY(run(c, PSPEC_K_SUMS, cat_bytes(r), [&] { launch_catalog_partials(ar, N, part_r, pl.nblk_sum, c->stream); }));
+  TRY(run(c, PSPEC_K_SUMS, 0.0, [&] { launch_catalog_final(part_d, pl.nblk_sum, part_r, pl.nblk_sum, der, c->stream); }));
+  const int nb = 8 * c->nsm;
+  const double nm = c->p.interlaced ? 2.0 : 1.0;
+  const double bd = cat_bytes(d) + (d->count ? nm * pl.Sr * 0.5 : 0.0);
+  const double br = cat_bytes(r) + nm * pl.Sr * 0.5;
+  if (d->count > 0)
+    TRY(run(c, PSPEC_K_PAINT, bd, [&] { launch_paint<T>(ad, c->p.window, c->p.interlaced, 0, der, m1, m2, N, nb, c->stream); }));
+  TRY(run(c, PSPEC_K_PAINT, br, [&] { launch_paint<T>(ar, c->p.window, c->p.interlaced, 1, der, m1, m2, N, nb, c->stream); }));
+  c->bytes_paint = cat_bytes(d) * 2 + cat_bytes(r) * 2 + nm * pl.Sr;
+  return PSPEC_OK;
+}
+
+template <typename T>
+pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, double* P, double* km, double* nm) {
+  using C = cx<T>;
+  const Plan& pl = c->pl;
+  const Geo& g = pl.g;
+  const int N = g.N;
+  cudaStream_t s = c->stream;
+  T* m1 = c->at<T>(pl.o_mesh1);
+  T* m2 = c->at<T>(pl.o_mesh2);
+  C* F0 = c->at<C>(pl.o_f0);
+  C* W = c->at<C>(pl.o_w);
+  T* f = pl.roundtrip ? c->at<T>(pl.o_f) : m1;
+  C* G = c->at<C>(pl.o_g);
+  const C* twh = c->at<C>(pl.o_twh);
+  const C* twf = c->at<C>(pl.o_twf);
+  const C* twr = c->at<C>(pl.o_twr);
+  const T* axis = c->at<T>(pl.o_axis);
+  const C* phase = c->at<C>(pl.o_phase);
+  const T* invw = c->at<T>(pl.o_invw);
+  const double Sr = (double)pl.Sr, Sc = (double)pl.Sc;
+  const int nslots = SLOT_ELL0 + n_ells;
+  BinTabs bt;
+  bt.bin_of_n2 = c->at<int32_t>(pl.o_bin);
+  bt.kmag_of_n2 = c->at<double>(pl.o_kmag);
+  bt.nk = nk;
+  bt.nslots = nslots;
+  bt.partials = c->at<double>(pl.o_part);
+  cudaError_t e = cudaMemsetAsync(bt.partials, 0, (size_t)pl.ctas_max * nslots * nk * sizeof(double), s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "partials clear");
+  int64_t transforms = 0;
+  double bytes = 0;
+  auto acc = [&](double b) { bytes += b; return b; };
+
+  // a3: F1 (and F2), combine + compensate -> F0, l = 0 bins; round trip -> f
+  TRY(run(c, PSPEC_K_FFT_Z, acc(Sr + Sc), [&] { launch_r2c_z<T>(m1, F0, g, pl.pz, twh, twr, pl.rows_z, s); }));
+  TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { launch_fft_y<T>(F0, 0, 1, g, pl.pf, twf, pl.tw_y, -1, s); }));
+  transforms++;
+  bt.ctas = pl.ctas_comb;
+  if (c->p.interlaced) {
+    TRY(run(c, PSPEC_K_FFT_X, acc(2 * Sc), [&] { launch_fft_x<T>(F0, F0, g, pl.pf, twf, pl.tw_x, -1, s); }));
+    TRY(run(c, PSPEC_K_FFT_Z, acc(Sr + Sc), [&] { launch_r2c_z<T>(m2, W, g, pl.pz, twh, twr, pl.rows_z, s); }));
+    TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { launch_fft_y<T>(W, 0, 1, g, pl.pf, twf, pl.tw_y, -1, s); }));
+    transforms++;
+    TRY(run(c, PSPEC_K_COMBINE, acc(3 * Sc), [&] {
+      launch_combine_x<T>(W, F0, g, pl.pf, twf, pl.tw_comb, 1, c->p.compensate, pl.roundtrip, phase, invw, bt, s);
+    }));
+  } else {
+    TRY(run(c, PSPEC_K_COMBINE, acc(2 * Sc), [&] {
+      launch_combine_x<T>(F0, F0, g, pl.pf, twf, pl.tw_comb, 0, c->p.compensate, pl.roundtrip, phase, invw, bt, s);
+    }));
+  }
+  if (pl.roundtrip) {
+    TRY(run(c, PSPEC_K_FFT_X, acc(2 * Sc), [&] { launch_fft_x<T>(F0, W, g, pl.pf, twf, pl.tw_x, +1, s); }));
+    TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { launch_fft_y<T>(W, 0, 1, g, pl.pf, twf, pl.tw_y, +1, s); }));
+    const T scale = T(2.0 / ((double)N * N * N));
+    TRY(run(c, PSPEC_K_C2R_Z, acc(Sc + Sr), [&] { launch_c2r_z<T>(W, f, g, pl.pz, twh, twr, pl.rows_z, scale, s); }));
+    transforms++;
+  }
+
+  // a4 + a5: per multipole l >= 2, groups of harmonics
+  int64_t sh = 0;
+  bt.ctas = pl.ctas_bin;
+  for (int i = 0; i < n_ells; i++) {
+    const int ell = ells[i];
+    sh += 2 * ell + 1;
+    if (ell == 0) continue;
+    const int nh = 2 * ell + 1;
+    for (int h0 = 0; h0 < nh; h0 += pl.group_max) {
+      const int M = std::min(pl.group_max, nh - h0);
+      int rows = std::max(1, pow2_floor(std::max(1, 2048 / (M * g.NH))));
+      while (rows > 1 && ((int64_t)N * N % rows || (pl.esz == 4 ? smem_ylm_z<float>(g, M, rows) : smem_ylm_z<double>(g, M, rows)) > kSmemBudget))
+        rows >>= 1;
+      const int64_t stride = (int64_t)N * N * g.NH;
+      TRY(run(c, PSPEC_K_YLM_Z, acc(Sr + M * Sc), [&] {
+        launch_ylm_r2c_z<T>(f, G, stride, ell, h0, M, g, pl.pz, twh, twr, axis, rows, s);
+      }));
+      TRY(run(c, PSPEC_K_FFT_Y, acc(2 * M * Sc), [&] { launch_fft_y<T>(G, stride, M, g, pl.pf, twf, pl.tw_y, -1, s); }));
+      TRY(run(c, PSPEC_K_BIN_X, acc(Sc + M * Sc), [&] {
+        launch_bin_x<T>(G, stride, ell, h0, M, F0, g, pl.pf, twf, pl.tw_bin, SLOT_ELL0 + i, bt, s);
+      }));
+      transforms += M;
+    }
+  }
+  // a6
+  TRY(run(c, PSPEC_K_FINAL, 0.0, [&] {
+    launch_finalize(bt.partials, pl.ctas_max, nslots, nk, ells, n_ells, c->at<double>(pl.o_derived), P, km, nm, s);
+  }));
+  c->transforms_last = transforms;
+  c->sh_last = sh;
+  c->bytes_mult = bytes;
+  return PSPEC_OK;
+}
+
+pspec_status check_ells_edges(Ctx* c, const int32_t* ells, int n_ells, const double* k_edges, int nk) {
+  if (!ells || n_ells < 1 || n_ells > kMaxElls) { c->err = "need 1..9 multipoles"; return PSPEC_EINVAL; }
+  for (int i = 0; i < n_ells; i++) {
+    if (ells[i] < 0) { c->err = "negative l"; return PSPEC_EINVAL; }
+    if (ells[i] & 1) { c->err = "odd l is not computed (parity)"; return PSPEC_EUNSUPPORTED; }
+    if (ells[i] > c->p.ell_max) { c->err = "l above the context's ell_max"; return PSPEC_EUNSUPPORTED; }
+    for (int j = 0; j < i; j++)
+      if (ells[j] == ells[i]) { c->err = "repeated l"; return PSPEC_EINVAL; }
+  }
+  if (!k_edges || nk < 1 || nk > c->max_kbins) { c->err = "n_kbins out of range"; return PSPEC_EINVAL; }
+  for (int b = 0; b <= nk; b++) {
+    if (!std::isfinite(k_edges[b]) || k_edges[b] < 0) { c->err = "k edges must be finite and >= 0"; return PSPEC_EINVAL; }
+    if (b && !(k_edges[b] > k_edges[b - 1])) { c->err = "k edges must increase strictly"; return PSPEC_EINVAL; }
+  }
+  if (!c->painted) { c->err = "multipoles before paint"; return PSPEC_ESTATE; }
+  return PSPEC_OK;
+}
+
+pspec_status multipoles_common(Ctx* c, const int32_t* ells, int n_ells, const double* k_edges, int nk,
+                               double* P, double* km, double* nm) {
+  TRY(check_ells_edges(c, ells, n_ells, k_edges, nk));
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  TRY(upload_bins(c, k_edges, nk));
+  if (c->p.precision == PSPEC_FP64) return do_multipoles<double>(c, ells, n_ells, nk, P, km, nm);
+  return do_multipoles<float>(c, ells, n_ells, nk, P, km, nm);
+}
+
+}  // namespace
+
+extern "C" {
+
+pspec_status pspec_workspace_size(const pspec_params* p, int32_t max_kbins, int64_t* bytes) {
+  if (!bytes) return PSPEC_EINVAL;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return PSPEC_ECUDA;
+  Plan pl;
+  std::string why;
+  pspec_status st = build_plan(p, max_kbins, nsm, &pl, &why);
+  if (st != PSPEC_OK) return st;
+  *bytes = (int64_t)pl.total;
+  return PSPEC_OK;
+}
+
+pspec_status pspec_create(const pspec_params* p, int32_t device, void* stream, void* workspace,
+                          int64_t workspace_bytes, int32_t max_kbins, void** out) {
+  if (!out) return PSPEC_EINVAL;
+  *out = nullptr;
+  if (cudaSetDevice(device) != cudaSuccess) return PSPEC_ECUDA;
+  int nsm = 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return PSPEC_ECUDA;
+  Ctx* c = new Ctx();
+  std::string why;
+  pspec_status st = build_plan(p, max_kbins, nsm, &c->pl, &why);
+  if (st != PSPEC_OK) {
+    delete c;
+    return st;
+  }
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % kAlign) || workspace_bytes < (int64_t)c->pl.total) {
+    delete c;
+    return workspace_bytes < (int64_t)c->pl.total ? PSPEC_ENOMEM : PSPEC_EINVAL;
+  }
+  c->p = *p;
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->ws = static_cast<char*>(workspace);
+  c->ws_bytes = workspace_bytes;
+  c->max_kbins = max_kbins;
+  c->nsm = nsm;
+  cudaError_t e = upload_ylm_tables(c->stream);
+  if (e != cudaSuccess) {
+    delete c;
+    return PSPEC_ECUDA;
+  }
+  st = c->p.precision == PSPEC_FP64 ? upload_tables<double>(c) : upload_tables<float>(c);
+  if (st != PSPEC_OK) {
+    delete c;
+    return st;
+  }
+  *out = c;
+  return PSPEC_OK;
+}
+
+pspec_status pspec_destroy(void* ctx) {
+  if (!ctx) return PSPEC_EINVAL;
+  Ctx* c = static_cast<Ctx*>(ctx);
+  for (auto& r : c->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto ev : c->pool) cudaEventDestroy(ev);
+  delete c;
+  return PSPEC_OK;
+}
+
+pspec_status pspec_paint(void* ctx, const pspec_catalog* data, const pspec_catalog* randoms, pspec_stats* stats) {
+  if (!ctx) return PSPEC_EINVAL;
+  Ctx* c = static_cast<Ctx*>(ctx);
+  TRY(check_catalog(c, data, "data", false));
+  TRY(check_catalog(c, randoms, "randoms", true));
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  pspec_status st = c->p.precision == PSPEC_FP64 ? do_paint<double>(c, data, randoms) : do_paint<float>(c, data, randoms);
+  if (st != PSPEC_OK) return st;
+  c->painted = true;
+  if (stats) {
+    double d[D_COUNT];
+    e = cudaMemcpyAsync(d, c->at<double>(c->pl.o_derived), sizeof(d), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stats copy");
+    stats->alpha = d[D_ALPHA];
+    stats->I = d[D_I];
+    stats->S = d[D_S];
+    stats->W_d = d[D_WD];
+    stats->W_r = d[D_WR];
+    stats->n_nonfinite = (int64_t)d[D_NONFINITE];
+    stats->n_wrapped = (int64_t)d[D_WRAPPED];
+    if (stats->n_nonfinite > 0) {
+      c->err = "non-finite position, weight or nbar in the catalogs";
+      c->painted = false;
+      return PSPEC_EINVAL;
+    }
+    if (!(d[D_WR] > 0)) {
+      c->err = "randoms completeness weights sum to zero";
+      c->painted = false;
+      return PSPEC_EINVAL;
+    }
+  }
+  return PSPEC_OK;
+}
+
+pspec_status pspec_multipoles(void* ctx, const int32_t* ells, int32_t n_ells, const double* k_edges,
+                              int32_t n_kbins, double* P, double* k_mean, double* n_modes) {
+  if (!ctx) return PSPEC_EINVAL;
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!P || !k_mean || !n_modes) { c->err = "output pointers are NULL"; return PSPEC_EINVAL; }
+  double* out = c->at<double>(c->pl.o_out);
+  const int nk = n_kbins;
+  TRY(multipoles_common(c, ells, n_ells, k_edges, nk, out + 2 * (size_t)nk, out, out + nk));
+  std::vector<double> h((size_t)(n_ells + 2) * nk);
+  cudaError_t e = cudaMemcpyAsync(h.data(), out, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "multipoles");
+  std::memcpy(k_mean, h.data(), nk * sizeof(double));
+  std::memcpy(n_modes, h.data() + nk, nk * sizeof(double));
+  std::memcpy(P, h.data() + 2 * (size_t)nk, (size_t)n_ells * nk * sizeof(double));
+  return PSPEC_OK;
+}
+
+pspec_status pspec_multipoles_device(void* ctx, const int32_t* ells, int32_t n_ells, const double* k_edges,
+                                     int32_t n_kbins, double* P_dev, double* k_mean_dev, double* n_modes_dev) {
+  if (!ctx) return PSPEC_EINVAL;
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!P_dev || !k_mean_dev || !n_modes_dev) { c->err = "output pointers are NULL"; return PSPEC_EINVAL; }
+  return multipoles_common(c, ells, n_ells, k_edges, n_kbins, P_dev, k_mean_dev, n_modes_dev);
+}
+
+pspec_status pspec_wedges(const double* P, const int32_t* ells, int32_t n_ells, int32_t n_kbins,
+                          const double* mu_edges, int32_t n_mu, double* out, void* stream) {
+  if (!P || !ells || !mu_edges || !out) return PSPEC_EINVAL;
+  if (n_ells < 1 || n_ells > kMaxElls || n_kbins < 1 || n_mu < 1 || n_mu > PSPEC_MAX_MU) return PSPEC_EINVAL;
+  for (int w = 0; w <= n_mu; w++) {
+    if (!std::isfinite(mu_edges[w]) || mu_edges[w] < 0.0 || mu_edges[w] > 1.0) return PSPEC_EINVAL;
+    if (w && !(mu_edges[w] > mu_edges[w - 1])) return PSPEC_EINVAL;
+  }
+  for (int i = 0; i < n_ells; i++) {
+    if (ells[i] < 0 || ells[i] > PSPEC_MAX_ELL) return PSPEC_EINVAL;
+    if (ells[i] & 1) return PSPEC_EUNSUPPORTED;
+  }
+  // Lbar_l(a, b) = [L_{l+1} - L_{l-1}]_a^b / ((2l+1)(b - a)), Lbar_0 = 1 (Sec. 2.2 eq. Lbar)
+  auto legendre = [](int l, double x) {
+    if (l == 0) return 1.0;
+    double p0 = 1.0, p1 = x;
+    for (int k = 2; k <= l; k++) {
+      const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    return p1;
+  };
+  WedgeTab t;
+  for (int i = 0; i < n_ells; i++) {
+    const int l = ells[i];
+    for (int w = 0; w < n_mu; w++) {
+      const double a = mu_edges[w], b = mu_edges[w + 1];
+      double v = 1.0;
+      if (l > 0) v = ((legendre(l + 1, b) - legendre(l - 1, b)) - (legendre(l + 1, a) - legendre(l - 1, a))) /
+                     ((2.0 * l + 1.0) * (b - a));
+      t.lbar[i * n_mu + w] = v;
+    }
+  }
+  launch_wedges(P, n_ells, n_kbins, n_mu, t, out, static_cast<cudaStream_t>(stream));
+  return cudaGetLastError() == cudaSuccess ? PSPEC_OK : PSPEC_ECUDA;
+}
+
+pspec_status pspec_get_plan_info(void* ctx, pspec_plan_info* info) {
+  if (!ctx || !info) return PSPEC_EINVAL;
+  Ctx* c = static_cast<Ctx*>(ctx);
+  info->nmesh = c->p.nmesh;
+  info->precision = c->p.precision;
+  info->ell_max = c->p.ell_max;
+  info->tile_y = c->pl.tw_y;
+  info->tile_x = c->pl.tw_x;
+  info->tile_bin = c->pl.tw_bin;
+  info->rows_z = c->pl.rows_z;
+  info->group_max = c->pl.group_max;
+  info->bin_ctas = c->pl.ctas_bin;
+  info->sh_transforms = c->sh_last;
+  info->transforms_executed = c->transforms_last;
+  info->kernel_launches = c->launches;
+  info->model_bytes_last = c->bytes_paint + c->bytes_mult;
+  return PSPEC_OK;
+}
+
+pspec_status pspec_set_profiling(void* ctx, int32_t enable) {
+  if (!ctx) return PSPEC_EINVAL;
+  static_cast<Ctx*>(ctx)->prof = enable != 0;
+  return PSPEC_OK;
+}
+
+pspec_status pspec_kernel_times(void* ctx, int64_t* launches, double* ms, double* bytes) {
+  if (!ctx) return PSPEC_EINVAL;
+  Ctx* c = static_cast<Ctx*>(ctx);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "kernel times");
+  for (auto& r : c->recs) {
+    float t = 0.f;
+    cudaEventElapsedTime(&t, r.a, r.b);
+    c->k_launch[r.k]++;
+    c->k_ms[r.k] += t;
+    c->k_bytes[r.k] += r.bytes;
+    c->pool.push_back(r.a);
+    c->pool.push_back(r.b);
+  }
+  c->recs.clear();
+  for (int k = 0; k < PSPEC_K_COUNT; k++) {
+    if (launches) launches[k] = c->k_launch[k];
+    if (ms) ms[k] = c->k_ms[k];
+    if (bytes) bytes[k] = c->k_bytes[k];
+    c->k_launch[k] = 0;
+    c->k_ms[k] = 0;
+    c->k_bytes[k] = 0;
+  }
+  return PSPEC_OK;
+}
+
+const char* pspec_kernel_name(int32_t k) {
+  static const char* names[PSPEC_K_COUNT] = {"catalog_sums", "paint", "r2c_z", "fft_y", "fft_x", "combine_x",
+                                             "ylm_r2c_z", "bin_x", "c2r_z", "finalize", "other"};
+  return (k >= 0 && k < PSPEC_K_COUNT) ? names[k] : "unknown";
+}
+
+const char* pspec_strerror(pspec_status s) {
+  switch (s) {
+    case PSPEC_OK: return "ok";
+    case PSPEC_EINVAL: return "invalid argument";
+    case PSPEC_ENOMEM: return "workspace too small";
+    case PSPEC_ECUDA: return "CUDA error";
+    case PSPEC_ETIMEOUT: return "device wait timed out";
+    case PSPEC_ECANCELED: return "cancelled";
+    case PSPEC_EUNSUPPORTED: return "unsupported";
+    case PSPEC_ESTATE: return "call out of order";
+    default: return "unknown status";
+  }
+}
+
+const char* pspec_last_error(void* ctx) {
+  if (!ctx) return "no context";
+  return static_cast<Ctx*>(ctx)->err.c_str();
+}
+
+const char* pspec_version(void) { return "libpspec 0.1 sm_103a"; }
+
+}  // extern "C"

@@ -1,0 +1,249 @@
+"""ctypes binding of libpspec (include/pspec.h): argument marshalling only.
+
+Every step of the estimator runs in the library's CUDA kernels. PyTorch supplies device
+memory (the workspace and the catalogs) and the CUDA stream. If libpspec.so is missing the
+binding raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libpspec.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ECANCELED, EUNSUPPORTED, ESTATE = range(8)
+WINDOWS = {"cic": 2, "tsc": 3}
+PRECISIONS = {"fp32": 0, "fp64": 1}
+K_NAMES = ["catalog_sums", "paint", "r2c_z", "fft_y", "fft_x", "combine_x", "ylm_r2c_z", "bin_x",
+           "c2r_z", "finalize", "other"]
+
+
+class PspecError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"pspec status {status}: {msg}")
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [("nmesh", C.c_int32), ("window", C.c_int32), ("interlaced", C.c_int32),
+                ("compensate", C.c_int32), ("precision", C.c_int32), ("ell_max", C.c_int32),
+                ("box_size", C.c_double), ("box_corner", C.c_double * 3), ("observer", C.c_double * 3),
+                ("P0", C.c_double), ("nbar", C.c_double), ("max_group_bytes", C.c_int64)]
+
+
+class Catalog(C.Structure):
+    _fields_ = [("pos", C.c_void_p), ("pos_dtype", C.c_int32), ("weight", C.c_void_p),
+                ("nbar", C.c_void_p), ("count", C.c_int64)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("alpha", C.c_double), ("I", C.c_double), ("S", C.c_double), ("W_d", C.c_double),
+                ("W_r", C.c_double), ("n_nonfinite", C.c_int64), ("n_wrapped", C.c_int64)]
+
+
+class PlanInfo(C.Structure):
+    _fields_ = [("nmesh", C.c_int32), ("precision", C.c_int32), ("ell_max", C.c_int32),
+                ("tile_y", C.c_int32), ("tile_x", C.c_int32), ("tile_bin", C.c_int32), ("rows_z", C.c_int32),
+                ("group_max", C.c_int32), ("bin_ctas", C.c_int32), ("sh_transforms", C.c_int64),
+                ("transforms_executed", C.c_int64), ("kernel_launches", C.c_int64),
+                ("model_bytes_last", C.c_double)]
+
+
+_lib = None
+
+# (name, restype, argtypes) for every entry point of include/pspec.h
+SIGNATURES = [
+    ("pspec_workspace_size", C.c_int32, [C.POINTER(Params), C.c_int32, C.POINTER(C.c_int64)]),
+    ("pspec_create", C.c_int32, [C.POINTER(Params), C.c_int32, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
+                                 C.POINTER(C.c_void_p)]),
+    ("pspec_destroy", C.c_int32, [C.c_void_p]),
+    ("pspec_paint", C.c_int32, [C.c_void_p, C.POINTER(Catalog), C.POINTER(Catalog), C.POINTER(Stats)]),
+    ("pspec_multipoles", C.c_int32, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_double),
+                                     C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                     C.POINTER(C.c_double)]),
+    ("pspec_multipoles_device", C.c_int32, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32,
+                                            C.POINTER(C.c_double), C.c_int32, C.c_void_p, C.c_void_p,
+                                            C.c_void_p]),
+    ("pspec_wedges", C.c_int32, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32, C.c_int32,
+                                 C.POINTER(C.c_double), C.c_int32, C.c_void_p, C.c_void_p]),
+    ("pspec_get_plan_info", C.c_int32, [C.c_void_p, C.POINTER(PlanInfo)]),
+    ("pspec_set_profiling", C.c_int32, [C.c_void_p, C.c_int32]),
+    ("pspec_kernel_times", C.c_int32, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double),
+                                       C.POINTER(C.c_double)]),
+    ("pspec_kernel_name", C.c_char_p, [C.c_int32]),
+    ("pspec_strerror", C.c_char_p, [C.c_int32]),
+    ("pspec_last_error", C.c_char_p, [C.c_void_p]),
+    ("pspec_version", C.c_char_p, []),
+]
+
+
+def load(path: str = LIB_PATH):
+    """Load libpspec.so and declare its signatures. Raises if it is not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_1704_02357_gb300.build`")
+    lib = C.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st: int, ctx=None):
+    if st != OK:
+        lib = load()
+        detail = lib.pspec_last_error(ctx).decode() if ctx else ""
+        raise PspecError(st, f"{lib.pspec_strerror(st).decode()} {detail}".strip())
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else int(t.data_ptr())
+
+
+def _dev_tensor(x, dtype, device, name):
+    import torch
+    if x is None:
+        return None
+    if not isinstance(x, torch.Tensor):
+        x = torch.as_tensor(np.ascontiguousarray(x))
+    if x.dtype != dtype:
+        x = x.to(dtype)
+    return x.to(device).contiguous()
+
+
+def _catalog(pos, weight, nbar, device, keep):
+    import torch
+    p = pos if isinstance(pos, torch.Tensor) else torch.as_tensor(np.ascontiguousarray(pos))
+    if p.dim() != 2 or p.shape[1] != 3:
+        raise ValueError("positions must be (n, 3)")
+    if p.dtype not in (torch.float64, torch.float32):
+        p = p.to(torch.float64)
+    p = p.to(device).contiguous()
+    w = _dev_tensor(weight, torch.float64, device, "weight")
+    nb = _dev_tensor(nbar, torch.float64, device, "nbar")
+    keep.extend([p, w, nb])
+    return Catalog(_ptr(p) if p.numel() else None, 1 if p.dtype == torch.float32 else 0, _ptr(w), _ptr(nb),
+                   int(p.shape[0]))
+
+
+class Estimator:
+    """One estimator context: a mesh geometry, window and precision, on one device/stream."""
+
+    def __init__(self, nmesh: int, box_size: float, box_corner, observer=(0.0, 0.0, 0.0), window="cic",
+                 interlaced=False, compensate=True, precision="fp32", ell_max=4, P0=0.0, nbar=0.0,
+                 max_group_bytes=0, max_kbins=512, device=None, stream=None):
+        import torch
+        lib = load()
+        self.device = torch.device(device if device is not None else "cuda", )
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.params = Params(int(nmesh), WINDOWS[window], int(bool(interlaced)), int(bool(compensate)),
+                             PRECISIONS[precision], int(ell_max), float(box_size),
+                             (C.c_double * 3)(*box_corner), (C.c_double * 3)(*observer), float(P0), float(nbar),
+                             int(max_group_bytes))
+        self.max_kbins = int(max_kbins)
+        nbytes = C.c_int64(0)
+        with torch.cuda.device(self.device):
+            _check(lib.pspec_workspace_size(C.byref(self.params), self.max_kbins, C.byref(nbytes)))
+            self.workspace_bytes = int(nbytes.value)
+            self._ws = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device=self.device)
+        base = self._ws.data_ptr()
+        self._ws_ptr = (base + 255) // 256 * 256
+        ctx = C.c_void_p()
+        _check(lib.pspec_create(C.byref(self.params), self.device.index, C.c_void_p(self.stream.cuda_stream),
+                                C.c_void_p(self._ws_ptr), self.workspace_bytes, self.max_kbins, C.byref(ctx)))
+        self._ctx = ctx
+        self._keep = []
+
+    # ------------------------------------------------------------------ a1 + a2
+    def paint(self, data_pos, randoms_pos, data_weight=None, data_nbar=None, randoms_weight=None,
+              randoms_nbar=None, stats=True):
+        lib = load()
+        keep = []
+        d = _catalog(data_pos, data_weight, data_nbar, self.device, keep)
+        r = _catalog(randoms_pos, randoms_weight, randoms_nbar, self.device, keep)
+        self._keep = keep  # inputs must outlive the enqueued kernels
+        st = Stats()
+        _check(lib.pspec_paint(self._ctx, C.byref(d), C.byref(r), C.byref(st) if stats else None), self._ctx)
+        if not stats:
+            return None
+        return {f: getattr(st, f) for f, _ in Stats._fields_}
+
+    # ------------------------------------------------------------------ a3..a6
+    def multipoles(self, ells: Sequence[int], k_edges) -> dict:
+        lib = load()
+        ells = [int(e) for e in ells]
+        edges = np.ascontiguousarray(k_edges, dtype=np.float64)
+        nk = len(edges) - 1
+        el = (C.c_int32 * len(ells))(*ells)
+        P = np.empty((len(ells), nk))
+        km = np.empty(nk)
+        nm = np.empty(nk)
+        dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+        _check(lib.pspec_multipoles(self._ctx, el, len(ells), dp(edges), nk, dp(P), dp(km), dp(nm)), self._ctx)
+        return {"P": P, "k_mean": km, "n_modes": nm, "ells": ells}
+
+    def multipoles_device(self, ells: Sequence[int], k_edges, P_out, kmean_out, nmodes_out):
+        """Enqueue without synchronising; outputs are float64 CUDA tensors (n_ells*nk, nk, nk)."""
+        lib = load()
+        ells = [int(e) for e in ells]
+        edges = np.ascontiguousarray(k_edges, dtype=np.float64)
+        el = (C.c_int32 * len(ells))(*ells)
+        _check(lib.pspec_multipoles_device(self._ctx, el, len(ells), edges.ctypes.data_as(C.POINTER(C.c_double)),
+                                           len(edges) - 1, C.c_void_p(_ptr(P_out)), C.c_void_p(_ptr(kmean_out)),
+                                           C.c_void_p(_ptr(nmodes_out))), self._ctx)
+
+    def plan_info(self) -> dict:
+        info = PlanInfo()
+        _check(load().pspec_get_plan_info(self._ctx, C.byref(info)), self._ctx)
+        return {f: getattr(info, f) for f, _ in PlanInfo._fields_}
+
+    def set_profiling(self, on: bool):
+        _check(load().pspec_set_profiling(self._ctx, int(bool(on))), self._ctx)
+
+    def kernel_times(self) -> dict:
+        n = len(K_NAMES)
+        la = (C.c_int64 * n)()
+        ms = (C.c_double * n)()
+        by = (C.c_double * n)()
+        _check(load().pspec_kernel_times(self._ctx, la, ms, by), self._ctx)
+        return {K_NAMES[k]: {"launches": la[k], "ms": ms[k], "bytes": by[k]} for k in range(n)}
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            load().pspec_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def wedges(P, ells: Sequence[int], mu_edges, stream=None):
+    """P(k, mu) wedges from multipoles (a float64 CUDA tensor (n_ells, nk)); returns (n_mu, nk)."""
+    import torch
+    lib = load()
+    P = P.contiguous()
+    if P.dtype != torch.float64 or not P.is_cuda:
+        raise ValueError("P must be a float64 CUDA tensor")
+    mu = np.ascontiguousarray(mu_edges, dtype=np.float64)
+    ells = [int(e) for e in ells]
+    n_mu = len(mu) - 1
+    out = torch.empty((n_mu, P.shape[1]), dtype=torch.float64, device=P.device)
+    s = stream if stream is not None else torch.cuda.current_stream(P.device)
+    el = (C.c_int32 * len(ells))(*ells)
+    _check(lib.pspec_wedges(C.c_void_p(P.data_ptr()), el, len(ells), int(P.shape[1]),
+                            mu.ctypes.data_as(C.POINTER(C.c_double)), n_mu, C.c_void_p(out.data_ptr()),
+                            C.c_void_p(s.cuda_stream)))
+    return out
