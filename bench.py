@@ -1,0 +1,464 @@
+"""Benchmark of the SH-FFT multipole estimator on one GB300 (or N, one catalog per GPU).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+One step = the whole hot path on one survey-shaped catalog resident in HBM: catalog sums
+and painting (data + 20x randoms, CIC, interlaced), the two forward transforms, the
+interlace + compensate combine, the inverse transform, 2l+1 Y_lm-weighted transforms per
+multipole with the accumulate-and-bin pass, finalisation (l = 0, 2, 4) and the wedges.
+Prints one JSON line (rank 0). Meshes (0.54 GB each) are larger than L2, so no flush is
+needed between steps.
+
+The catalog: a lognormal field with P(k) = 2e4 (k/0.02)/(1 + (k/0.02)^2.4), Poisson
+sampled at n̄ = 3e-4, moved into redshift space radially (f = 0.75), cut to a 60-degree cap
+and a 600-1400 Mpc/h shell inside a 2000 Mpc/h box; randoms 20x uniform in the cap;
+FKP P0 = 1e4; 512^3 mesh; k bins of 0.005 h/Mpc up to the Nyquist frequency.
+
+--impl reference times the FP64 CPU oracle (as it stands) on the host cores instead, on a
+bounded sample of the same workload: each step measures one full 512^3 oracle transform
+and 1/64 slices of its painting, harmonic evaluations and binning; a set's time is composed
+from those measured costs. It needs no GPU; under torchrun only rank 0 runs it.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "P_ℓ(k) sets/s at 512³, ℓmax=4/16, FP32 batched vs FP64 plain; p50/p99 latency"
+NMESH = 512
+BOX = 2000.0
+NBAR = 3e-4
+P0 = 1e4
+ELLS = [0, 2, 4]
+ELLS16 = list(range(0, 17, 2))
+MU_EDGES = [0.0, 0.05, 0.2, 0.4, 0.6, 0.8, 1.0]
+WORKLOAD = ("survey cap (60 deg, 600-1400 Mpc/h) lognormal catalog, nbar 3e-4 (~7.9e5 data, 20x randoms), "
+            "512^3 mesh over 2000 Mpc/h, CIC + interlacing + compensation, l = 0,2,4, FP32 mesh/FFT, FP64 sums/bins")
+
+
+def k_edges(nmesh=NMESH, box=BOX, dk=0.005):
+    kn = math.pi * nmesh / box
+    n = int(kn / dk)
+    return dk * np.arange(n + 1)
+
+
+def workload(seed_offset=0):
+    import synth
+    geo = synth.survey_geometry(box_size=BOX)
+    fld = synth.lognormal_field(256, geo.box_size, geo.box_corner, seed=3 + 1000 * seed_offset)
+    data = synth.survey_catalog(fld, geo, nbar=NBAR, seed=33 + 1000 * seed_offset)
+    randoms = synth.survey_randoms(20 * data.size, geo, seed=4 + 1000 * seed_offset)
+    return geo, data, randoms
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = (uuid or "").lower()
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            if self.uuid and self.uuid not in parts[0].lower():
+                continue
+            try:
+                mhz.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+# --------------------------------------------------------------------------- peaks
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(p))["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it still matches the source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        t = json.load(open(p))
+    except (OSError, ValueError):
+        return None
+    ent = t.get("kernels", {}).get(kernel)
+    if not ent or ent.get("source_hash") != source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1704_02357_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+# --------------------------------------------------------------------------- oracle baseline
+def oracle_components(data, randoms, frac, fft=True):
+    """Measured oracle costs (seconds) at 512^3: a 1/frac slice of painting, of the real- and
+    k-space harmonic evaluations and of one binning pass, plus one full rfftn."""
+    import scipy.fft as sfft
+    from oracle import estimator as E
+
+    p = E.Params(nmesh=NMESH, box_size=BOX, box_corner=_corner(), window="cic", interlaced=True,
+                 compensate=True, P0=P0, nbar=NBAR)
+    rng = np.random.default_rng(0)
+    out = {}
+    # painting: two meshes (interlaced), a random 1/frac of all particles
+    allpos = np.concatenate([data.pos, randoms.pos])
+    sel = rng.choice(allpos.shape[0], size=max(1, allpos.shape[0] // frac), replace=False)
+    vals = np.ones(sel.size)
+    t = time.perf_counter()
+    E.paint(allpos[sel], vals, p)
+    E.paint(allpos[sel], vals, p, shift=0.5)
+    out["paint"] = (time.perf_counter() - t) * allpos.shape[0] / sel.size
+    # real-space harmonic weights on 1/frac of the planes
+    nplane = max(1, NMESH // frac)
+    ix = np.arange(nplane)
+    t = time.perf_counter()
+    ux, uy, uz = E.node_rhat(p, ix)
+    E.real_ylm(2, 1, ux, uy, uz)
+    out["ylm_r"] = (time.perf_counter() - t) * NMESH / nplane
+    # k-space harmonic on 1/frac of the modes, product with F0 and accumulation
+    n_modes = NMESH * NMESH * (NMESH // 2 + 1)
+    m = max(1, n_modes // frac)
+    kv = rng.standard_normal((3, m))
+    kv /= np.linalg.norm(kv, axis=0)
+    g = rng.standard_normal(m) + 1j * rng.standard_normal(m)
+    f0 = rng.standard_normal(m) + 1j * rng.standard_normal(m)
+    acc = np.zeros(m)
+    t = time.perf_counter()
+    acc += E.real_ylm(2, 1, *kv) * np.real(g * np.conj(f0))
+    out["ylm_k"] = (time.perf_counter() - t) * n_modes / m
+    b = rng.integers(-1, 160, size=m)
+    t = time.perf_counter()
+    s = b >= 0
+    np.bincount(b[s], weights=acc[s], minlength=160)
+    out["bin"] = (time.perf_counter() - t) * n_modes / m
+    if fft:
+        x = rng.standard_normal((NMESH,) * 3)
+        t = time.perf_counter()
+        sfft.rfftn(x, workers=E._workers())
+        out["fft"] = time.perf_counter() - t
+        del x
+    return out
+
+
+def _corner():
+    import synth
+    return tuple(float(c) for c in synth.survey_geometry(box_size=BOX).box_corner)
+
+
+def oracle_set_seconds(c, ells=ELLS):
+    """One set: paint + F1, F2 and the inverse transform + per harmonic (weights, transform,
+    k-space harmonic) + one binning pass per multipole."""
+    nh = sum(2 * l + 1 for l in ells if l > 0)
+    return c["paint"] + 3 * c["fft"] + nh * (c["ylm_r"] + c["fft"] + c["ylm_k"]) + len(ells) * c["bin"]
+
+
+def oracle_cores():
+    from oracle import estimator as E
+    return E._workers()
+
+
+def cpu_baseline(data, randoms):
+    c = oracle_components(data, randoms, frac=64)
+    sec = oracle_set_seconds(c)
+    return {"value": 1.0 / sec, "unit": "sets/s", "cores": oracle_cores(), "kind": "oracle",
+            "sample": ("FP64 NumPy/SciPy oracle at 512^3, l=0,2,4, composed from measured costs: one full "
+                       "scipy rfftn, and 1/64 slices of the painting (2 interlaced meshes), the real- and "
+                       "k-space Y_lm evaluations with the F0 product, and one binning pass; "
+                       f"set = paint + 3 transforms + 14 x (Y_r + transform + Y_k) + 3 binnings = {sec:.1f} s"),
+            "components_s": {k: round(v, 3) for k, v in c.items()}}
+
+
+def run_reference(args):
+    ws, rank, local = dist_setup()
+    if rank != 0:
+        return 0
+    geo, data, randoms = workload(0)
+    budget = 240.0
+    t_start = time.perf_counter()
+    for _ in range(args.warmup):
+        oracle_components(data, randoms, frac=256)
+    per_set = []
+    steps = 0
+    for _ in range(args.steps):
+        c = oracle_components(data, randoms, frac=64)
+        per_set.append(oracle_set_seconds(c))
+        steps += 1
+        if time.perf_counter() - t_start > budget:
+            break
+    sec = statistics.median(per_set)
+    value = 1.0 / sec
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "sets/s", "n_gpus": args.gpus,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": 1000.0 * sec, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (FP64 CPU oracle)", "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "sets/s", "cores": oracle_cores(), "kind": "oracle",
+                             "sample": "per step: one full 512^3 oracle rfftn and 1/64 slices of painting, "
+                                       "harmonic evaluations and binning; set time composed from them"},
+            "e2e": {"value": value, "unit": "sets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="skip the l<=16 and FP64 side measurements")
+    ap.add_argument("--nmesh", type=int, default=NMESH, help="mesh side (512 is the benchmark; smaller for ncu captures)")
+    ap.add_argument("--ells", default="0,2,4", help="multipoles of the headline measurement")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    from paper_1704_02357_gb300 import Estimator, wedges
+    geo, data, randoms = workload(rank)
+    nmesh = args.nmesh
+    ells_main = [int(x) for x in args.ells.split(",")]
+    edges = k_edges(nmesh)
+    nk = len(edges) - 1
+    corner = tuple(geo.box_corner)
+    stream = torch.cuda.current_stream(dev)
+
+    def est_for(precision, ell_max):
+        return Estimator(nmesh=nmesh, box_size=BOX, box_corner=corner, observer=(0.0, 0.0, 0.0), window="cic",
+                         interlaced=True, compensate=True, precision=precision, ell_max=ell_max, P0=P0, nbar=NBAR,
+                         max_kbins=nk, device=dev, stream=stream)
+
+    dpos = torch.as_tensor(data.pos, device=dev)
+    rpos = torch.as_tensor(randoms.pos, device=dev)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(est, ells, steps, warmup, profile=False):
+        P = torch.empty(len(ells) * nk, dtype=torch.float64, device=dev)
+        km = torch.empty(nk, dtype=torch.float64, device=dev)
+        nm = torch.empty(nk, dtype=torch.float64, device=dev)
+
+        def step():
+            est.paint(dpos, rpos, stats=False)
+            est.multipoles_device(ells, edges, P, km, nm)
+            wedges(P.view(len(ells), nk), ells, MU_EDGES, stream=stream)
+
+        for _ in range(warmup):
+            step()
+        barrier()
+        if profile:
+            est.kernel_times()          # drop warm-up records
+            est.set_profiling(True)
+        l0 = est.plan_info()["kernel_launches"]
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        launches = est.plan_info()["kernel_launches"] - l0 + steps   # + one wedge kernel per step
+        kt = None
+        if profile:
+            est.set_profiling(False)
+            kt = est.kernel_times()
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, launches, kt, P
+
+    # ---- headline: FP32, l = 0, 2, 4
+    est = est_for("fp32", max(ells_main))
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    with ClockSampler(uuid) as clk:
+        ms, launches, kt, P = timed(est, ells_main, args.steps, args.warmup, profile=True)
+    clocks = clk.summary()
+    ms_step = ms / args.steps
+    value = ws * args.steps / (ms / 1000.0)
+    info = est.plan_info()
+
+    # dominant kernel and its roofline
+    peak, peak_kind = hbm_peak()
+    dom = max(kt.items(), key=lambda kv: kv[1]["ms"])
+    dname, d = dom
+    achieved = (d["bytes"] / 1e9) / (d["ms"] / 1e3) if d["ms"] > 0 else 0.0
+    per_kernel = {k: {"launches": v["launches"], "ms_total": round(v["ms"], 3),
+                      "share": round(v["ms"] / sum(x["ms"] for x in kt.values()), 4),
+                      "GBps": round((v["bytes"] / 1e9) / (v["ms"] / 1e3), 1) if v["ms"] > 0 and v["bytes"] else None}
+                  for k, v in kt.items() if v["launches"]}
+    total_bytes = info["model_bytes_last"]
+
+    # ---- e2e: host-resident catalogs (pinned), copied in every step; results read back
+    dh = torch.as_tensor(data.pos).pin_memory()
+    rh = torch.as_tensor(randoms.pos).pin_memory()
+    e2e_steps = max(3, min(args.steps, 10))
+
+    def e2e_step():
+        dpos.copy_(dh, non_blocking=True)
+        rpos.copy_(rh, non_blocking=True)
+        est.paint(dpos, rpos, stats=False)
+        out = est.multipoles(ells_main, edges)  # synchronises and copies the result to the host
+        return out
+
+    for _ in range(2):
+        e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    barrier()
+    t_e2e = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([t_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e = {"value": ws * e2e_steps / t_e2e, "unit": "sets/s",
+           "h2d_bytes_per_step": int(dh.numel() * 8 + rh.numel() * 8),
+           "d2h_bytes_per_step": int((len(ells_main) + 2) * nk * 8)}
+
+    side = {}
+    if not args.quick:
+        # ---- l <= 16 (153 transforms by the paper's count), FP32
+        e16 = est_for("fp32", 16)
+        ms16, _, _, _ = timed(e16, ELLS16, max(3, args.steps // 4), 3)
+        side["ell_max_16_fp32"] = {"value": ws * max(3, args.steps // 4) / (ms16 / 1000.0), "unit": "sets/s",
+                                   "ms_per_set": ms16 / max(3, args.steps // 4)}
+        e16.close()
+        # ---- plain FP64 path, l = 0, 2, 4
+        e64 = est_for("fp64", 4)
+        ms64, _, _, _ = timed(e64, ELLS, max(3, args.steps // 4), 3)
+        side["fp64_plain_ell_max_4"] = {"value": ws * max(3, args.steps // 4) / (ms64 / 1000.0), "unit": "sets/s",
+                                        "ms_per_set": ms64 / max(3, args.steps // 4)}
+        e64.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and nmesh == NMESH:
+        del dh, rh
+        cpu = cpu_baseline(data, randoms)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "sets/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD if (nmesh == NMESH and ells_main == ELLS) else
+                       f"{WORKLOAD} [run at {nmesh}^3, l = {ells_main}]", "nmesh": nmesh, "ells": ells_main, "n_data": int(data.size),
+                       "n_randoms": int(randoms.size), "k_bins": nk,
+                       "l2": "inputs larger than L2 (0.54 GB meshes, 0.4 GB particles); no flush",
+                       "parallelism": f"{ws} GPU(s), one independent catalog per GPU"},
+            "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_kind,
+                         "traffic": traffic_for(dname),
+                         "algorithmic_bytes_per_launch": d["bytes"] / max(1, d["launches"])},
+            "step_roofline": {"model_bytes_per_set": total_bytes,
+                              "achieved_GBps": total_bytes / 1e9 / (ms_step / 1e3),
+                              "frac": total_bytes / 1e9 / (ms_step / 1e3) / peak},
+            "kernels": per_kernel,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "plan": {k: info[k] for k in ("tile_y", "tile_x", "tile_bin", "rows_z", "group_max", "bin_ctas",
+                                          "sh_transforms", "transforms_executed")},
+            "cpu_baseline": cpu,
+        }
+        line.update(side)
+        print(json.dumps(line), flush=True)
+    est.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

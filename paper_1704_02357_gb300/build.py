@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpspec.so")
 SOURCES = ["k_fft.cu", "k_misc.cu", "pspec_api.cu"]
-HEADERS = ["common.cuh", "launch.h"]
+HEADERS = ["common.cuh", "fft_engine.cuh", "launch.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -14,18 +14,26 @@ using namespace pspec;
 namespace {
 
 constexpr size_t kAlign = 256;
-constexpr size_t kSmemBudget = 200 * 1024;
+constexpr size_t kSmemBudget = 200 * 1024;   // one block
+constexpr size_t kSmemShared = 100 * 1024;   // two blocks per SM
 constexpr int kMaxElls = PSPEC_MAX_ELL / 2 + 1;
+constexpr int kYlmThreads = 256;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
+// N even, 2^a (N >= 16) or 3*2^a (N >= 48), N <= 1024: the register FFT holds 8 (24)
+// elements per thread and needs N/2 >= 8 (24).
 bool good_nmesh(int n) {
-  if (n < 8 || n > 1024 || (n & 1)) return false;
+  if (n < 16 || n > 1024 || (n & 1)) return false;
   int x = n;
   while ((x & 1) == 0) x >>= 1;
-  return x == 1 || x == 3;
+  if (x == 1) return true;
+  return x == 3 && n >= 48;
 }
 
+int elems_per_thread(int N) { return N % 3 == 0 ? 24 : 8; }
+
+// Radices dividing E, largest first; the factor 3 (if any) last.
 FftPlan make_fft(int L) {
   FftPlan p{};
   p.L = L;
@@ -37,10 +45,18 @@ FftPlan make_fft(int L) {
     p.nst++;
     x /= r;
   };
-  while (x % 3 == 0) push(3);
+  int three = 0;
+  while (x % 3 == 0) {
+    x /= 3;
+    three++;
+  }
   while (x % 8 == 0) push(8);
   while (x % 4 == 0) push(4);
   while (x % 2 == 0) push(2);
+  for (int i = 0; i < three; i++) {
+    x *= 3;
+    push(3);
+  }
   return p;
 }
 
@@ -52,32 +68,38 @@ int pow2_floor(int v) {
 
 struct Plan {
   Geo g;
-  int esz;          // sizeof(T)
+  int E;
+  int esz;  // sizeof(T)
+  size_t csz;
   FftPlan pz, pf;
-  int tw_y, tw_x, tw_comb, tw_bin, rows_z;
-  int group_max;
-  int ctas_comb, ctas_bin, ctas_max;
+  int tw_y, tw_comb, tw_bin, rows_z;
+  int group_max, ylm_rows_max;
+  int ctas_comb, ctas_bin;
   int nblk_sum;
-  int nslots_max;
   bool roundtrip;
   size_t Sr, Sc;
-  // workspace offsets
-  size_t o_mesh1, o_mesh2, o_f0, o_w, o_f, o_g, o_twh, o_twf, o_twr, o_axis, o_phase, o_invw, o_bin,
-      o_kmag, o_sums, o_derived, o_part, o_out, total;
   int n2max;
+  // workspace offsets
+  size_t o_mesh1, o_mesh2, o_f0, o_w, o_f, o_g, o_twh, o_twf, o_twr, o_axis, o_phase, o_invw, o_bin, o_kmag, o_cnt,
+      o_lo, o_hi, o_nmodes, o_ksum, o_sums, o_derived, o_bins, o_out, total;
 };
 
-template <typename T> size_t cx_size() { return sizeof(cx<T>); }
-
-int pick_tw(int NH, size_t per_tw_bytes, size_t fixed, size_t budget, int max_tw) {
-  for (int tw = max_tw; tw >= 1; tw >>= 1)
-    if (NH % tw == 0 && fixed + per_tw_bytes * (size_t)tw <= budget) return tw;
+// Column tiles: TW kz columns x N/E threads each, at most 1024 threads (512 preferred) and
+// the shared-memory budget.
+int pick_tw(const Plan& pl, int per_col_bytes, size_t fixed, size_t budget, int max_threads) {
+  const int N = pl.g.N, NH = pl.g.NH, Tc = N / pl.E;
+  for (int tw = 16; tw >= 1; tw >>= 1) {
+    if (NH % tw) continue;
+    if (tw * Tc > max_threads) continue;
+    if (fixed + (size_t)per_col_bytes * tw > budget) continue;
+    return tw;
+  }
   return 1;
 }
 
 pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl, std::string* why) {
   if (!p) { *why = "params is NULL"; return PSPEC_EINVAL; }
-  if (!good_nmesh(p->nmesh)) { *why = "nmesh must be even, 8..1024, 2^a or 3*2^a"; return PSPEC_EUNSUPPORTED; }
+  if (!good_nmesh(p->nmesh)) { *why = "nmesh must be even, 16..1024 and 2^a, or 48..768 and 3*2^a"; return PSPEC_EUNSUPPORTED; }
   if (p->window != PSPEC_WINDOW_CIC && p->window != PSPEC_WINDOW_TSC) { *why = "window must be CIC or TSC"; return PSPEC_EINVAL; }
   if (p->precision != PSPEC_FP32 && p->precision != PSPEC_FP64) { *why = "precision must be FP32 or FP64"; return PSPEC_EINVAL; }
   if (p->ell_max < 0 || (p->ell_max & 1)) { *why = "ell_max must be even and >= 0"; return PSPEC_EUNSUPPORTED; }
@@ -93,43 +115,49 @@ pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl,
   const int N = p->nmesh, NH = N / 2;
   pl->g.N = N;
   pl->g.NH = NH;
+  pl->E = elems_per_thread(N);
   pl->esz = f64 ? 8 : 4;
-  const size_t csz = f64 ? 16 : 8;
+  pl->csz = f64 ? 16 : 8;
+  const size_t csz = pl->csz;
   pl->pz = make_fft(NH);
   pl->pf = make_fft(N);
   pl->roundtrip = p->interlaced || p->compensate;
   pl->Sr = (size_t)N * N * N * pl->esz;
   pl->Sc = (size_t)N * N * NH * csz;
-
-  const size_t budget2 = 110 * 1024;   // two CTAs per SM
-  pl->tw_y = pick_tw(NH, 2 * N * csz, N * csz, budget2, 16);
-  pl->tw_x = pl->tw_y;
-  pl->tw_comb = pick_tw(NH, 2 * N * csz, N * csz + 3 * (size_t)max_kbins * 8, budget2, 16);
-  pl->tw_bin = pick_tw(NH, 3 * N * csz + N * pl->esz, N * csz + (size_t)max_kbins * 8, budget2, 8);
-  if (pl->tw_bin < 1) pl->tw_bin = 1;
-  pl->rows_z = std::max(1, pow2_floor(std::max(1, 2048 / NH)));
-  while ((int64_t)N * N % pl->rows_z) pl->rows_z >>= 1;
-
-  const int nharm = 2 * p->ell_max + 1;
-  int m_smem = (int)((kSmemBudget / csz - 2 * (size_t)NH) / (2 * (size_t)NH));
-  int m_mem = p->max_group_bytes > 0 ? (int)(p->max_group_bytes / (int64_t)pl->Sc) : nharm;
-  pl->group_max = std::max(1, std::min(nharm, std::min(m_smem, m_mem)));
-  if (p->ell_max == 0) pl->group_max = 0;
-
-  if (f64) {
-    pl->ctas_comb = combine_x_ctas<double>(pl->g, pl->tw_comb, nsm, max_kbins);
-    pl->ctas_bin = bin_x_ctas<double>(pl->g, pl->tw_bin, nsm, max_kbins);
-  } else {
-    pl->ctas_comb = combine_x_ctas<float>(pl->g, pl->tw_comb, nsm, max_kbins);
-    pl->ctas_bin = bin_x_ctas<float>(pl->g, pl->tw_bin, nsm, max_kbins);
-  }
-  pl->ctas_max = std::max(pl->ctas_comb, pl->ctas_bin);
-  pl->nblk_sum = 2 * nsm;
-  pl->nslots_max = SLOT_ELL0 + kMaxElls;
   pl->n2max = 3 * NH * NH;
 
+  const size_t bins_bytes = (size_t)max_kbins * (8 + pl->esz * 32);  // FP64 bins + up to 32 warps of partials
+  pl->tw_y = pick_tw(*pl, N * (int)csz, 0, kSmemShared, 512);
+  pl->tw_comb = pick_tw(*pl, N * (int)csz, bins_bytes, kSmemBudget, 512);
+  pl->tw_bin = pick_tw(*pl, 2 * N * (int)csz, bins_bytes, kSmemBudget, 512);
+  const int Tz = NH / pl->E;
+  pl->rows_z = std::max(1, pow2_floor(std::max(1, 512 / Tz)));
+  while (pl->rows_z > 1 && (((int64_t)N * N) % pl->rows_z || smem_rows(NH, pl->rows_z, csz) > kSmemShared))
+    pl->rows_z >>= 1;
+
+  // harmonics per group: staging of M rows of N reals + the exchange buffer
+  const int nharm = 2 * p->ell_max + 1;
+  const int spr = kYlmThreads / Tz;
+  const size_t xb = smem_rows(NH, spr, csz);
+  int m_smem = (int)((kSmemBudget - xb) / ((size_t)N * pl->esz));
+  int m_mem = p->max_group_bytes > 0 ? (int)(p->max_group_bytes / (int64_t)pl->Sc) : nharm;
+  pl->group_max = p->ell_max == 0 ? 0 : std::max(1, std::min(nharm, std::min(m_smem, m_mem)));
+
+  if (f64) {
+    pl->ctas_comb = persistent_ctas<double>(0, pl->g, pl->E, pl->tw_comb, max_kbins, nsm);
+    pl->ctas_bin = persistent_ctas<double>(1, pl->g, pl->E, pl->tw_bin, max_kbins, nsm);
+  } else {
+    pl->ctas_comb = persistent_ctas<float>(0, pl->g, pl->E, pl->tw_comb, max_kbins, nsm);
+    pl->ctas_bin = persistent_ctas<float>(1, pl->g, pl->E, pl->tw_bin, max_kbins, nsm);
+  }
+  pl->nblk_sum = 2 * nsm;
+
   size_t o = 0;
-  auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes); return at; };
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align_up(o + bytes);
+    return at;
+  };
   pl->o_mesh1 = take(pl->Sr);
   pl->o_mesh2 = p->interlaced ? take(pl->Sr) : 0;
   pl->o_f0 = take(pl->Sc);
@@ -144,9 +172,14 @@ pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl,
   pl->o_invw = take((N + NH) * (size_t)pl->esz);
   pl->o_bin = take((pl->n2max + 1) * sizeof(int32_t));
   pl->o_kmag = take((pl->n2max + 1) * sizeof(double));
+  pl->o_cnt = take((pl->n2max + 1) * sizeof(uint32_t));
+  pl->o_lo = take(max_kbins * sizeof(int32_t));
+  pl->o_hi = take(max_kbins * sizeof(int32_t));
+  pl->o_nmodes = take(max_kbins * sizeof(double));
+  pl->o_ksum = take(max_kbins * sizeof(double));
   pl->o_sums = take(2 * (size_t)pl->nblk_sum * kSumVals * sizeof(double));
   pl->o_derived = take(D_COUNT * sizeof(double));
-  pl->o_part = take((size_t)pl->ctas_max * pl->nslots_max * max_kbins * sizeof(double));
+  pl->o_bins = take((size_t)(SLOT_ELL0 + kMaxElls) * max_kbins * sizeof(double));
   pl->o_out = take(((size_t)kMaxElls + 2) * max_kbins * sizeof(double));
   pl->total = o;
   return PSPEC_OK;
@@ -170,7 +203,11 @@ struct Ctx {
   double bytes_paint = 0, bytes_mult = 0;
   // profiling
   bool prof = false;
-  struct Rec { int k; cudaEvent_t a, b; double bytes; };
+  struct Rec {
+    int k;
+    cudaEvent_t a, b;
+    double bytes;
+  };
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
   int64_t k_launch[PSPEC_K_COUNT] = {};
@@ -214,10 +251,10 @@ pspec_status run(Ctx* c, int kclass, double bytes, F&& launch) {
   return PSPEC_OK;
 }
 
-#define TRY(x)                       \
-  do {                               \
-    pspec_status _s = (x);           \
-    if (_s != PSPEC_OK) return _s;   \
+#define TRY(x)                     \
+  do {                             \
+    pspec_status _s = (x);         \
+    if (_s != PSPEC_OK) return _s; \
   } while (0)
 
 pspec_status cuda_fail(Ctx* c, cudaError_t e, const char* what) {
@@ -245,7 +282,7 @@ pspec_status upload_tables(Ctx* c) {
   const double H = c->p.box_size / N;
   for (int d = 0; d < 3; d++)
     for (int i = 0; i < N; i++) axis[d * N + i] = T(c->p.box_corner[d] + i * H - c->p.observer[d]);
-  const int p = c->p.window;  // sinc order
+  const int p = c->p.window;  // order of sinc^p
   auto sincp = [&](int n) {
     if (n == 0) return 1.0;
     const double x = M_PI * n / N;
@@ -264,12 +301,17 @@ pspec_status upload_tables(Ctx* c) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->at<T>(pl.o_axis), axis.data(), 3 * N * sizeof(T), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->at<C>(pl.o_phase), phase.data(), (N + NH) * sizeof(C), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->at<T>(pl.o_invw), invw.data(), (N + NH) * sizeof(T), cudaMemcpyHostToDevice, c->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->at<uint32_t>(pl.o_cnt), 0, (pl.n2max + 1) * sizeof(uint32_t), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "table upload");
+  TRY(run(c, PSPEC_K_OTHER, 0.0, [&] { launch_mode_counts(pl.g, c->at<uint32_t>(pl.o_cnt), c->nsm, c->stream); }));
+  e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "table upload");
   return PSPEC_OK;
 }
 
 // Bin decision of every |n|^2 in FP64: b iff t_b <= n2 < t_{b+1}, t_b = (k_b L/(2 pi))^2.
+// The |n|^2 values of a bin form one range [lo_b, hi_b); N_b and sum |k| follow on the
+// device from the mode counts.
 pspec_status upload_bins(Ctx* c, const double* edges, int nk) {
   std::vector<double> e(edges, edges + nk + 1);
   if (e == c->edges) return PSPEC_OK;
@@ -279,24 +321,35 @@ pspec_status upload_bins(Ctx* c, const double* edges, int nk) {
     const double x = e[b] * c->p.box_size / (2.0 * M_PI);
     t[b] = x * x;
   }
-  std::vector<int32_t> bin(pl.n2max + 1);
+  std::vector<int32_t> bin(pl.n2max + 1), lo(nk, 0), hi(nk, 0);
   std::vector<double> kmag(pl.n2max + 1);
   const double kf = 2.0 * M_PI / c->p.box_size;
   for (int n2 = 0; n2 <= pl.n2max; n2++) {
     const double x = (double)n2;
     int b = -1;
-    if (n2 > 0 && x >= t[0] && x < t[nk]) {
-      b = (int)(std::upper_bound(t.begin(), t.end(), x) - t.begin()) - 1;
-    }
+    if (n2 > 0 && x >= t[0] && x < t[nk]) b = (int)(std::upper_bound(t.begin(), t.end(), x) - t.begin()) - 1;
     bin[n2] = b;
     kmag[n2] = kf * std::sqrt(x);
+    if (b >= 0) {
+      if (hi[b] == 0) lo[b] = n2;
+      hi[b] = n2 + 1;
+    }
   }
   cudaError_t er = cudaMemcpyAsync(c->at<int32_t>(pl.o_bin), bin.data(), bin.size() * sizeof(int32_t),
                                    cudaMemcpyHostToDevice, c->stream);
   if (er == cudaSuccess)
-    er = cudaMemcpyAsync(c->at<double>(pl.o_kmag), kmag.data(), kmag.size() * sizeof(double),
-                         cudaMemcpyHostToDevice, c->stream);
-  if (er == cudaSuccess) er = cudaStreamSynchronize(c->stream);
+    er = cudaMemcpyAsync(c->at<double>(pl.o_kmag), kmag.data(), kmag.size() * sizeof(double), cudaMemcpyHostToDevice,
+                         c->stream);
+  if (er == cudaSuccess)
+    er = cudaMemcpyAsync(c->at<int32_t>(pl.o_lo), lo.data(), nk * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream);
+  if (er == cudaSuccess)
+    er = cudaMemcpyAsync(c->at<int32_t>(pl.o_hi), hi.data(), nk * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream);
+  if (er != cudaSuccess) return cuda_fail(c, er, "bin table upload");
+  TRY(run(c, PSPEC_K_OTHER, 0.0, [&] {
+    launch_bin_counts(c->at<uint32_t>(pl.o_cnt), c->at<double>(pl.o_kmag), c->at<int32_t>(pl.o_lo),
+                      c->at<int32_t>(pl.o_hi), nk, c->at<double>(pl.o_nmodes), c->at<double>(pl.o_ksum), c->stream);
+  }));
+  er = cudaStreamSynchronize(c->stream);
   if (er != cudaSuccess) return cuda_fail(c, er, "bin table upload");
   c->edges = e;
   return PSPEC_OK;
@@ -311,6 +364,8 @@ pspec_status check_catalog(Ctx* c, const pspec_catalog* cat, const char* name, b
   return PSPEC_OK;
 }
 
+double fkp(double nbar, double P0) { return P0 > 0 ? 1.0 / (1.0 + nbar * P0) : 1.0; }
+
 PaintArgs paint_args(Ctx* c, const pspec_catalog* cat) {
   PaintArgs a;
   a.pos = cat->pos;
@@ -319,9 +374,10 @@ PaintArgs paint_args(Ctx* c, const pspec_catalog* cat) {
   a.nbar = cat->nbar;
   a.count = cat->count;
   for (int d = 0; d < 3; d++) a.corner[d] = c->p.box_corner[d];
-  a.cell = c->p.box_size / c->p.nmesh;
+  a.inv_cell = (double)c->p.nmesh / c->p.box_size;
   a.P0 = c->p.P0;
   a.nbar_default = c->p.nbar;
+  a.wf_default = fkp(c->p.nbar, c->p.P0);
   return a;
 }
 
@@ -340,22 +396,35 @@ pspec_status do_paint(Ctx* c, const pspec_catalog* d, const pspec_catalog* r) {
   cudaError_t e = cudaMemsetAsync(m1, 0, pl.Sr, c->stream);
   if (e == cudaSuccess && m2) e = cudaMemsetAsync(m2, 0, pl.Sr, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "mesh clear");
-  double* sums = c->at<double>(pl.o_sums);
-  double* part_d = sums;
-  double* part_r = sums + (size_t)pl.nblk_sum * kSumVals;
   double* der = c->at<double>(pl.o_derived);
   const PaintArgs ad = paint_args(c, d), ar = paint_args(c, r);
-  TRY(run(c, PSPEC_K_SUMS, cat_bytes(d), [&] { launch_catalog_partials(ad, N, part_d, pl.nblk_sum, c->stream); }));
-  TRY(run(c, PSPEC_K_SUMS, cat_bytes(r), [&] { launch_catalog_partials(ar, N, part_r, pl.nblk_sum, c->stream); }));
-  TRY(run(c, PSPEC_K_SUMS, 0.0, [&] { launch_catalog_final(part_d, pl.nblk_sum, part_r, pl.nblk_sum, der, c->stream); }));
-  const int nb = 8 * c->nsm;
-  const double nm = c->p.interlaced ? 2.0 : 1.0;
-  const double bd = cat_bytes(d) + (d->count ? nm * pl.Sr * 0.5 : 0.0);
-  const double br = cat_bytes(r) + nm * pl.Sr * 0.5;
+  const bool uniform = !d->weight && !d->nbar && !r->weight && !r->nbar;
+  double bytes = 0;
+  if (uniform) {
+    TRY(run(c, PSPEC_K_SUMS, 0.0, [&] {
+      launch_derive_uniform(d->count, r->count, ad.wf_default, c->p.nbar, der, c->stream);
+    }));
+  } else {
+    double* sums = c->at<double>(pl.o_sums);
+    double* part_d = sums;
+    double* part_r = sums + (size_t)pl.nblk_sum * kSumVals;
+    TRY(run(c, PSPEC_K_SUMS, cat_bytes(d), [&] { launch_catalog_partials(ad, part_d, pl.nblk_sum, c->stream); }));
+    TRY(run(c, PSPEC_K_SUMS, cat_bytes(r), [&] { launch_catalog_partials(ar, part_r, pl.nblk_sum, c->stream); }));
+    TRY(run(c, PSPEC_K_SUMS, 0.0, [&] { launch_catalog_final(part_d, pl.nblk_sum, part_r, pl.nblk_sum, der, c->stream); }));
+    bytes += cat_bytes(d) + cat_bytes(r);
+  }
+  // algorithmic bytes of painting: the particles once and each mesh written once
+  const int nb = 16 * c->nsm;
+  const double nmesh = c->p.interlaced ? 2.0 : 1.0;
+  const double frac_d = (double)d->count / (double)(d->count + r->count);
   if (d->count > 0)
-    TRY(run(c, PSPEC_K_PAINT, bd, [&] { launch_paint<T>(ad, c->p.window, c->p.interlaced, 0, der, m1, m2, N, nb, c->stream); }));
-  TRY(run(c, PSPEC_K_PAINT, br, [&] { launch_paint<T>(ar, c->p.window, c->p.interlaced, 1, der, m1, m2, N, nb, c->stream); }));
-  c->bytes_paint = cat_bytes(d) * 2 + cat_bytes(r) * 2 + nm * pl.Sr;
+    TRY(run(c, PSPEC_K_PAINT, cat_bytes(d) + frac_d * nmesh * pl.Sr, [&] {
+      launch_paint<T>(ad, c->p.window, c->p.interlaced, 0, der, m1, m2, N, nb, c->stream);
+    }));
+  TRY(run(c, PSPEC_K_PAINT, cat_bytes(r) + (1.0 - frac_d) * nmesh * pl.Sr, [&] {
+    launch_paint<T>(ar, c->p.window, c->p.interlaced, 1, der, m1, m2, N, nb, c->stream);
+  }));
+  c->bytes_paint = bytes + cat_bytes(d) + cat_bytes(r) + nmesh * pl.Sr;
   return PSPEC_OK;
 }
 
@@ -364,7 +433,7 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
   using C = cx<T>;
   const Plan& pl = c->pl;
   const Geo& g = pl.g;
-  const int N = g.N;
+  const int N = g.N, E = pl.E;
   cudaStream_t s = c->stream;
   T* m1 = c->at<T>(pl.o_mesh1);
   T* m2 = c->at<T>(pl.o_mesh2);
@@ -379,48 +448,49 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
   const C* phase = c->at<C>(pl.o_phase);
   const T* invw = c->at<T>(pl.o_invw);
   const double Sr = (double)pl.Sr, Sc = (double)pl.Sc;
-  const int nslots = SLOT_ELL0 + n_ells;
-  BinTabs bt;
-  bt.bin_of_n2 = c->at<int32_t>(pl.o_bin);
-  bt.kmag_of_n2 = c->at<double>(pl.o_kmag);
-  bt.nk = nk;
-  bt.nslots = nslots;
-  bt.partials = c->at<double>(pl.o_part);
-  cudaError_t e = cudaMemsetAsync(bt.partials, 0, (size_t)pl.ctas_max * nslots * nk * sizeof(double), s);
-  if (e != cudaSuccess) return cuda_fail(c, e, "partials clear");
+  BinArgs ba;
+  ba.bin_of_n2 = c->at<int32_t>(pl.o_bin);
+  ba.nk = nk;
+  ba.bins = c->at<double>(pl.o_bins);
+  cudaError_t e = cudaMemsetAsync(ba.bins, 0, (size_t)(SLOT_ELL0 + n_ells) * nk * sizeof(double), s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "bins clear");
   int64_t transforms = 0;
   double bytes = 0;
-  auto acc = [&](double b) { bytes += b; return b; };
+  auto acc = [&](double b) {
+    bytes += b;
+    return b;
+  };
 
-  // a3: F1 (and F2), combine + compensate -> F0, l = 0 bins; round trip -> f
-  TRY(run(c, PSPEC_K_FFT_Z, acc(Sr + Sc), [&] { launch_r2c_z<T>(m1, F0, g, pl.pz, twh, twr, pl.rows_z, s); }));
-  TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { launch_fft_y<T>(F0, 0, 1, g, pl.pf, twf, pl.tw_y, -1, s); }));
+  // a3: F1 (and F2), combine + compensate -> F0 with the l = 0 sums; round trip -> f
+  TRY(run(c, PSPEC_K_FFT_Z, acc(Sr + Sc), [&] { launch_r2c_z<T>(m1, F0, g, pl.pz, E, twh, twr, pl.rows_z, s); }));
+  TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { launch_fft_y<T>(F0, 0, 1, g, pl.pf, E, twf, pl.tw_y, -1, s); }));
   transforms++;
-  bt.ctas = pl.ctas_comb;
   if (c->p.interlaced) {
-    TRY(run(c, PSPEC_K_FFT_X, acc(2 * Sc), [&] { launch_fft_x<T>(F0, F0, g, pl.pf, twf, pl.tw_x, -1, s); }));
-    TRY(run(c, PSPEC_K_FFT_Z, acc(Sr + Sc), [&] { launch_r2c_z<T>(m2, W, g, pl.pz, twh, twr, pl.rows_z, s); }));
-    TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { launch_fft_y<T>(W, 0, 1, g, pl.pf, twf, pl.tw_y, -1, s); }));
+    TRY(run(c, PSPEC_K_FFT_X, acc(2 * Sc), [&] { launch_fft_x<T>(F0, F0, g, pl.pf, E, twf, pl.tw_y, -1, s); }));
+    TRY(run(c, PSPEC_K_FFT_Z, acc(Sr + Sc), [&] { launch_r2c_z<T>(m2, W, g, pl.pz, E, twh, twr, pl.rows_z, s); }));
+    TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { launch_fft_y<T>(W, 0, 1, g, pl.pf, E, twf, pl.tw_y, -1, s); }));
     transforms++;
     TRY(run(c, PSPEC_K_COMBINE, acc(3 * Sc), [&] {
-      launch_combine_x<T>(W, F0, g, pl.pf, twf, pl.tw_comb, 1, c->p.compensate, pl.roundtrip, phase, invw, bt, s);
+      launch_combine_x<T>(W, F0, g, pl.pf, E, twf, pl.tw_comb, 1, c->p.compensate, pl.roundtrip, phase, invw, ba,
+                          pl.ctas_comb, s);
     }));
   } else {
     TRY(run(c, PSPEC_K_COMBINE, acc(2 * Sc), [&] {
-      launch_combine_x<T>(F0, F0, g, pl.pf, twf, pl.tw_comb, 0, c->p.compensate, pl.roundtrip, phase, invw, bt, s);
+      launch_combine_x<T>(F0, F0, g, pl.pf, E, twf, pl.tw_comb, 0, c->p.compensate, pl.roundtrip, phase, invw, ba,
+                          pl.ctas_comb, s);
     }));
   }
   if (pl.roundtrip) {
-    TRY(run(c, PSPEC_K_FFT_X, acc(2 * Sc), [&] { launch_fft_x<T>(F0, W, g, pl.pf, twf, pl.tw_x, +1, s); }));
-    TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { launch_fft_y<T>(W, 0, 1, g, pl.pf, twf, pl.tw_y, +1, s); }));
+    TRY(run(c, PSPEC_K_FFT_X, acc(2 * Sc), [&] { launch_fft_x<T>(F0, W, g, pl.pf, E, twf, pl.tw_y, +1, s); }));
+    TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { launch_fft_y<T>(W, 0, 1, g, pl.pf, E, twf, pl.tw_y, +1, s); }));
     const T scale = T(2.0 / ((double)N * N * N));
-    TRY(run(c, PSPEC_K_C2R_Z, acc(Sc + Sr), [&] { launch_c2r_z<T>(W, f, g, pl.pz, twh, twr, pl.rows_z, scale, s); }));
+    TRY(run(c, PSPEC_K_C2R_Z, acc(Sc + Sr), [&] { launch_c2r_z<T>(W, f, g, pl.pz, E, twh, twr, pl.rows_z, scale, s); }));
     transforms++;
   }
 
   // a4 + a5: per multipole l >= 2, groups of harmonics
   int64_t sh = 0;
-  bt.ctas = pl.ctas_bin;
+  const int64_t stride = (int64_t)N * N * g.NH;
   for (int i = 0; i < n_ells; i++) {
     const int ell = ells[i];
     sh += 2 * ell + 1;
@@ -428,23 +498,25 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
     const int nh = 2 * ell + 1;
     for (int h0 = 0; h0 < nh; h0 += pl.group_max) {
       const int M = std::min(pl.group_max, nh - h0);
-      int rows = std::max(1, pow2_floor(std::max(1, 2048 / (M * g.NH))));
-      while (rows > 1 && ((int64_t)N * N % rows || (pl.esz == 4 ? smem_ylm_z<float>(g, M, rows) : smem_ylm_z<double>(g, M, rows)) > kSmemBudget))
+      int rows = std::max(1, pow2_floor(std::max(1, 96 * 1024 / (M * N * pl.esz))));
+      while (rows > 1 && (((int64_t)N * N) % rows ||
+                          (pl.esz == 4 ? smem_ylm_z<float>(g, E, M, rows, kYlmThreads)
+                                       : smem_ylm_z<double>(g, E, M, rows, kYlmThreads)) > kSmemBudget))
         rows >>= 1;
-      const int64_t stride = (int64_t)N * N * g.NH;
       TRY(run(c, PSPEC_K_YLM_Z, acc(Sr + M * Sc), [&] {
-        launch_ylm_r2c_z<T>(f, G, stride, ell, h0, M, g, pl.pz, twh, twr, axis, rows, s);
+        launch_ylm_r2c_z<T>(f, G, stride, ell, h0, M, g, pl.pz, E, twh, twr, axis, rows, kYlmThreads, s);
       }));
-      TRY(run(c, PSPEC_K_FFT_Y, acc(2 * M * Sc), [&] { launch_fft_y<T>(G, stride, M, g, pl.pf, twf, pl.tw_y, -1, s); }));
+      TRY(run(c, PSPEC_K_FFT_Y, acc(2 * M * Sc), [&] { launch_fft_y<T>(G, stride, M, g, pl.pf, E, twf, pl.tw_y, -1, s); }));
       TRY(run(c, PSPEC_K_BIN_X, acc(Sc + M * Sc), [&] {
-        launch_bin_x<T>(G, stride, ell, h0, M, F0, g, pl.pf, twf, pl.tw_bin, SLOT_ELL0 + i, bt, s);
+        launch_bin_x<T>(G, stride, ell, h0, M, F0, g, pl.pf, E, twf, pl.tw_bin, SLOT_ELL0 + i, ba, pl.ctas_bin, s);
       }));
       transforms += M;
     }
   }
   // a6
   TRY(run(c, PSPEC_K_FINAL, 0.0, [&] {
-    launch_finalize(bt.partials, pl.ctas_max, nslots, nk, ells, n_ells, c->at<double>(pl.o_derived), P, km, nm, s);
+    launch_finalize(ba.bins, c->at<double>(pl.o_nmodes), c->at<double>(pl.o_ksum), nk, ells, n_ells,
+                    c->at<double>(pl.o_derived), P, km, nm, s);
   }));
   c->transforms_last = transforms;
   c->sh_last = sh;
@@ -470,8 +542,8 @@ pspec_status check_ells_edges(Ctx* c, const int32_t* ells, int n_ells, const dou
   return PSPEC_OK;
 }
 
-pspec_status multipoles_common(Ctx* c, const int32_t* ells, int n_ells, const double* k_edges, int nk,
-                               double* P, double* km, double* nm) {
+pspec_status multipoles_common(Ctx* c, const int32_t* ells, int n_ells, const double* k_edges, int nk, double* P,
+                               double* km, double* nm) {
   TRY(check_ells_edges(c, ells, n_ells, k_edges, nk));
   cudaError_t e = cudaSetDevice(c->device);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
@@ -497,8 +569,8 @@ pspec_status pspec_workspace_size(const pspec_params* p, int32_t max_kbins, int6
   return PSPEC_OK;
 }
 
-pspec_status pspec_create(const pspec_params* p, int32_t device, void* stream, void* workspace,
-                          int64_t workspace_bytes, int32_t max_kbins, void** out) {
+pspec_status pspec_create(const pspec_params* p, int32_t device, void* stream, void* workspace, int64_t workspace_bytes,
+                          int32_t max_kbins, void** out) {
   if (!out) return PSPEC_EINVAL;
   *out = nullptr;
   if (cudaSetDevice(device) != cudaSuccess) return PSPEC_ECUDA;
@@ -512,8 +584,9 @@ pspec_status pspec_create(const pspec_params* p, int32_t device, void* stream, v
     return st;
   }
   if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % kAlign) || workspace_bytes < (int64_t)c->pl.total) {
+    const bool small = workspace_bytes < (int64_t)c->pl.total;
     delete c;
-    return workspace_bytes < (int64_t)c->pl.total ? PSPEC_ENOMEM : PSPEC_EINVAL;
+    return small ? PSPEC_ENOMEM : PSPEC_EINVAL;
   }
   c->p = *p;
   c->device = device;
@@ -571,7 +644,7 @@ pspec_status pspec_paint(void* ctx, const pspec_catalog* data, const pspec_catal
     stats->n_nonfinite = (int64_t)d[D_NONFINITE];
     stats->n_wrapped = (int64_t)d[D_WRAPPED];
     if (stats->n_nonfinite > 0) {
-      c->err = "non-finite position, weight or nbar in the catalogs";
+      c->err = "invalid position, weight or nbar in the catalogs";
       c->painted = false;
       return PSPEC_EINVAL;
     }
@@ -584,8 +657,8 @@ pspec_status pspec_paint(void* ctx, const pspec_catalog* data, const pspec_catal
   return PSPEC_OK;
 }
 
-pspec_status pspec_multipoles(void* ctx, const int32_t* ells, int32_t n_ells, const double* k_edges,
-                              int32_t n_kbins, double* P, double* k_mean, double* n_modes) {
+pspec_status pspec_multipoles(void* ctx, const int32_t* ells, int32_t n_ells, const double* k_edges, int32_t n_kbins,
+                              double* P, double* k_mean, double* n_modes) {
   if (!ctx) return PSPEC_EINVAL;
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!P || !k_mean || !n_modes) { c->err = "output pointers are NULL"; return PSPEC_EINVAL; }
@@ -610,8 +683,8 @@ pspec_status pspec_multipoles_device(void* ctx, const int32_t* ells, int32_t n_e
   return multipoles_common(c, ells, n_ells, k_edges, n_kbins, P_dev, k_mean_dev, n_modes_dev);
 }
 
-pspec_status pspec_wedges(const double* P, const int32_t* ells, int32_t n_ells, int32_t n_kbins,
-                          const double* mu_edges, int32_t n_mu, double* out, void* stream) {
+pspec_status pspec_wedges(const double* P, const int32_t* ells, int32_t n_ells, int32_t n_kbins, const double* mu_edges,
+                          int32_t n_mu, double* out, void* stream) {
   if (!P || !ells || !mu_edges || !out) return PSPEC_EINVAL;
   if (n_ells < 1 || n_ells > kMaxElls || n_kbins < 1 || n_mu < 1 || n_mu > PSPEC_MAX_MU) return PSPEC_EINVAL;
   for (int w = 0; w <= n_mu; w++) {
@@ -639,8 +712,9 @@ pspec_status pspec_wedges(const double* P, const int32_t* ells, int32_t n_ells, 
     for (int w = 0; w < n_mu; w++) {
       const double a = mu_edges[w], b = mu_edges[w + 1];
       double v = 1.0;
-      if (l > 0) v = ((legendre(l + 1, b) - legendre(l - 1, b)) - (legendre(l + 1, a) - legendre(l - 1, a))) /
-                     ((2.0 * l + 1.0) * (b - a));
+      if (l > 0)
+        v = ((legendre(l + 1, b) - legendre(l - 1, b)) - (legendre(l + 1, a) - legendre(l - 1, a))) /
+            ((2.0 * l + 1.0) * (b - a));
       t.lbar[i * n_mu + w] = v;
     }
   }
@@ -655,7 +729,7 @@ pspec_status pspec_get_plan_info(void* ctx, pspec_plan_info* info) {
   info->precision = c->p.precision;
   info->ell_max = c->p.ell_max;
   info->tile_y = c->pl.tw_y;
-  info->tile_x = c->pl.tw_x;
+  info->tile_x = c->pl.tw_comb;
   info->tile_bin = c->pl.tw_bin;
   info->rows_z = c->pl.rows_z;
   info->group_max = c->pl.group_max;
@@ -724,6 +798,6 @@ const char* pspec_last_error(void* ctx) {
   return static_cast<Ctx*>(ctx)->err.c_str();
 }
 
-const char* pspec_version(void) { return "libpspec 0.1 sm_103a"; }
+const char* pspec_version(void) { return "libpspec 0.2 sm_103a"; }
 
 }  // extern "C"
