@@ -30,11 +30,23 @@ __host__ __device__ __forceinline__ int padded_len(int L) { return L + (L >> 4);
 
 template <typename C> __device__ __forceinline__ C ldg_c(const C* p) { return __ldg(p); }
 
-template <typename C, int E, int R, int LAYOUT>
+template <typename C, int E, int R, int LAYOUT, int DIR>
 __device__ __forceinline__ void stage_regs(C (&v)[E], C* sm, int t, int Tc, int L, int Ns, bool last, int seq,
-                                           int nseq, int Lp, const C* __restrict__ tw, int dir) {
+                                           int nseq, int Lp, const C* __restrict__ tw) {
   constexpr int Q = E / R;
   const int tstep = L / (Ns * R);
+  // When Ns divides Tc (both powers of two) every butterfly of this thread has the same
+  // k = t mod Ns, so with several butterflies (Q > 1) its R - 1 twiddles are loaded once.
+  const bool shared_k = (Q > 1) && (Ns > 1) && !last && (Ns <= Tc);
+  C ws[R > 1 && Q > 1 ? R : 1];
+  if constexpr (Q > 1) if (shared_k) {
+    const int k = t & (Ns - 1);
+#pragma unroll
+    for (int r = 1; r < R; r++) {
+      ws[r] = ldg_c(tw + r * k * tstep);
+      if (DIR > 0) ws[r].y = -ws[r].y;
+    }
+  }
 #pragma unroll
   for (int q = 0; q < Q; q++) {
     const int j = t + Tc * q;
@@ -42,15 +54,21 @@ __device__ __forceinline__ void stage_regs(C (&v)[E], C* sm, int t, int Tc, int 
     C u[R];
 #pragma unroll
     for (int r = 0; r < R; r++) u[r] = v[q + r * Q];
-    if (Ns > 1) {
+    if constexpr (Q > 1) {
+      if (shared_k) {
+#pragma unroll
+        for (int r = 1; r < R; r++) u[r] = cmul(u[r], ws[r]);
+      }
+    }
+    if (!shared_k && Ns > 1) {
 #pragma unroll
       for (int r = 1; r < R; r++) {
         C w = ldg_c(tw + r * k * tstep);
-        if (dir > 0) w.y = -w.y;
+        if (DIR > 0) w.y = -w.y;
         u[r] = cmul(u[r], w);
       }
     }
-    Dft<C, R>::run(u, dir);
+    Dft<C, R>::run(u, DIR);
     if (last) {
 #pragma unroll
       for (int r = 0; r < R; r++) v[q + r * Q] = u[r];
@@ -62,11 +80,12 @@ __device__ __forceinline__ void stage_regs(C (&v)[E], C* sm, int t, int Tc, int 
   }
 }
 
-// Transforms the sequence whose slots this thread holds. All threads of the block must call
-// it (it contains __syncthreads); the shared buffer is free again when it returns.
-template <typename C, int E, int LAYOUT>
+// Transforms the sequence whose slots this thread holds (DIR = -1 forward, +1 inverse).
+// All threads of the block must call it (it contains __syncthreads); the shared buffer is
+// free again when it returns.
+template <typename C, int E, int LAYOUT, int DIR>
 __device__ __forceinline__ void fft_regs(C (&v)[E], C* sm, const FftPlan& p, int t, int seq, int nseq,
-                                         const C* __restrict__ tw, int dir) {
+                                         const C* __restrict__ tw) {
   const int L = p.L;
   const int Tc = L / E;
   const int Lp = padded_len(L);
@@ -75,16 +94,16 @@ __device__ __forceinline__ void fft_regs(C (&v)[E], C* sm, const FftPlan& p, int
     const int Ns = p.ns[s];
     switch (p.rad[s]) {
       case 8:
-        if constexpr (E % 8 == 0) stage_regs<C, E, 8, LAYOUT>(v, sm, t, Tc, L, Ns, last, seq, nseq, Lp, tw, dir);
+        if constexpr (E % 8 == 0) stage_regs<C, E, 8, LAYOUT, DIR>(v, sm, t, Tc, L, Ns, last, seq, nseq, Lp, tw);
         break;
       case 4:
-        if constexpr (E % 4 == 0) stage_regs<C, E, 4, LAYOUT>(v, sm, t, Tc, L, Ns, last, seq, nseq, Lp, tw, dir);
+        if constexpr (E % 4 == 0) stage_regs<C, E, 4, LAYOUT, DIR>(v, sm, t, Tc, L, Ns, last, seq, nseq, Lp, tw);
         break;
       case 3:
-        if constexpr (E % 3 == 0) stage_regs<C, E, 3, LAYOUT>(v, sm, t, Tc, L, Ns, last, seq, nseq, Lp, tw, dir);
+        if constexpr (E % 3 == 0) stage_regs<C, E, 3, LAYOUT, DIR>(v, sm, t, Tc, L, Ns, last, seq, nseq, Lp, tw);
         break;
       default:
-        if constexpr (E % 2 == 0) stage_regs<C, E, 2, LAYOUT>(v, sm, t, Tc, L, Ns, last, seq, nseq, Lp, tw, dir);
+        if constexpr (E % 2 == 0) stage_regs<C, E, 2, LAYOUT, DIR>(v, sm, t, Tc, L, Ns, last, seq, nseq, Lp, tw);
         break;
     }
     if (!last) {

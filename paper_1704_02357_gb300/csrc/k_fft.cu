@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(512) k_r2c_z(const T* __restrict__ in, cx<T>* 
   C v[E];
 #pragma unroll
   for (int e = 0; e < E; e++) v[e] = src[t + Tc * e];
-  fft_regs<C, E, kPaddedRows>(v, sm, pz, t, r, rows, twh, -1);
+  fft_regs<C, E, kPaddedRows, -1>(v, sm, pz, t, r, rows, twh);
 #pragma unroll
   for (int e = 0; e < E; e++) sm[sidx<kPaddedRows>(r, t + Tc * e, rows, Lp)] = v[e];
   __syncthreads();
@@ -90,16 +90,18 @@ __global__ void __launch_bounds__(512) k_c2r_z(const cx<T>* __restrict__ in, T* 
     const C od = cmul(cscale(csub(xk, xm), T(0.5)), cconj(ldg_c(twr + k)));
     v[e] = mk(ev.x - od.y, ev.y + od.x);  // E + i O
   }
-  fft_regs<C, E, kPaddedRows>(v, sm, pz, t, r, rows, twh, +1);
+  fft_regs<C, E, kPaddedRows, +1>(v, sm, pz, t, r, rows, twh);
   C* dst = reinterpret_cast<C*>(out + row * g.N);
 #pragma unroll
   for (int e = 0; e < E; e++) dst[t + Tc * e] = cscale(v[e], scale);
 }
 
 // ------------------------------------------------------------------ pass z: Y_lm-weighted r2c
-// For `rows` rows of f, the M harmonics h0..h0+M-1 of multipole l: every point sweeps its
-// harmonics once ((x+iy)^a carried from one |m| to the next) into a shared staging area;
-// the M*rows sequences are then transformed, spr at a time, and unpacked to the spectra.
+// For `rows` rows of f and the M harmonics h0..h0+M-1 of multipole l. Every point sweeps
+// its harmonics once ((x+iy)^a carried from one |m| to the next) into a shared staging
+// area of nseq = M*rows real rows; then each of the nseq*Tc threads loads its slots, the
+// sequences are transformed (the staging area is reused as the exchange buffer) and
+// unpacked into the M spectra.
 template <typename T, int E>
 __global__ void __launch_bounds__(512) k_ylm_r2c_z(const T* __restrict__ f, cx<T>* __restrict__ out,
                                                   int64_t spec_stride, int ell, int h0, int M, Geo g, FftPlan pz,
@@ -108,10 +110,9 @@ __global__ void __launch_bounds__(512) k_ylm_r2c_z(const T* __restrict__ f, cx<T
   using C = cx<T>;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = g.N, L = g.NH, Tc = L / E, Lp = padded_len(L);
-  const int spr = blockDim.x / Tc;
   const int nseq = M * rows;
-  T* stage = reinterpret_cast<T*>(smraw);                         // [nseq][N] reals
-  C* xb = reinterpret_cast<C*>(smraw + (size_t)nseq * N * sizeof(T));  // [spr][Lp]
+  T* stage = reinterpret_cast<T*>(smraw);  // [nseq][N] reals, then the exchange buffer
+  C* xb = reinterpret_cast<C*>(smraw);
   const YTab<T>& yt = ytab<T>();
   const int64_t row0 = (int64_t)blockIdx.x * rows;
   const int a_lo = harm_a(h0), a_hi = harm_a(h0 + M - 1);
@@ -138,7 +139,7 @@ __global__ void __launch_bounds__(512) k_ylm_r2c_z(const T* __restrict__ f, cx<T
     for (int a = a_lo; a <= a_hi; a++) {
       const T q = fv * ylm_q<T>(yt, ell, a, z);
       if (a == 0) {
-        stage[(0 * rows + r) * N + kk] = q;
+        stage[r * N + kk] = q;
       } else {
         const int hp = 2 * a - 1, hm = 2 * a;
         if (hp >= h0 && hp < h0 + M) stage[((hp - h0) * rows + r) * N + kk] = sq2 * q * pr;
@@ -151,36 +152,30 @@ __global__ void __launch_bounds__(512) k_ylm_r2c_z(const T* __restrict__ f, cx<T
   }
   __syncthreads();
   const C* stc = reinterpret_cast<const C*>(stage);
-  const int sl = threadIdx.x / Tc, t = threadIdx.x - sl * Tc;
-  for (int base = 0; base < nseq; base += spr) {
-    const int sq = base + sl;
-    const bool live = sq < nseq;
-    C v[E];
+  const int sq = threadIdx.x / Tc, t = threadIdx.x - sq * Tc;
+  C v[E];
 #pragma unroll
-    for (int e = 0; e < E; e++) v[e] = live ? stc[sq * L + t + Tc * e] : mk(T(0), T(0));
-    fft_regs<C, E, kPaddedRows>(v, xb, pz, t, sl, spr, twh, -1);
+  for (int e = 0; e < E; e++) v[e] = stc[sq * L + t + Tc * e];
+  __syncthreads();
+  fft_regs<C, E, kPaddedRows, -1>(v, xb, pz, t, sq, nseq, twh);
 #pragma unroll
-    for (int e = 0; e < E; e++) xb[sidx<kPaddedRows>(sl, t + Tc * e, spr, Lp)] = v[e];
-    __syncthreads();
-    if (live) {
-      const int s = sq / rows, r = sq - s * rows;
-      C* dst = out + s * spec_stride + (row0 + r) * L;
+  for (int e = 0; e < E; e++) xb[sidx<kPaddedRows>(sq, t + Tc * e, nseq, Lp)] = v[e];
+  __syncthreads();
+  const int s = sq / rows, r = sq - s * rows;
+  C* dst = out + s * spec_stride + (row0 + r) * L;
 #pragma unroll
-      for (int e = 0; e < E; e++) {
-        const int k = t + Tc * e;
-        const C zm = xb[sidx<kPaddedRows>(sl, k ? L - k : 0, spr, Lp)];
-        dst[k] = r2c_unpack<C, T>(v[e], zm, ldg_c(twr + k));
-      }
-    }
-    __syncthreads();
+  for (int e = 0; e < E; e++) {
+    const int k = t + Tc * e;
+    const C zm = xb[sidx<kPaddedRows>(sq, k ? L - k : 0, nseq, Lp)];
+    dst[k] = r2c_unpack<C, T>(v[e], zm, ldg_c(twr + k));
   }
 }
 
 // ------------------------------------------------------------------ pass y (in place)
 // Block: one (i, kz-tile) slab, TW columns x Tc threads (column fastest).
-template <typename T, int E>
-__global__ void __launch_bounds__(512) k_fft_y(cx<T>* __restrict__ data, int64_t spec_stride, Geo g, FftPlan pf,
-                                               const cx<T>* __restrict__ twf, int TW, int dir) {
+template <typename T, int E, int DIR>
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_fft_y(cx<T>* __restrict__ data, int64_t spec_stride, Geo g, FftPlan pf,
+                                                  const cx<T>* __restrict__ twf, int TW) {
   using C = cx<T>;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
@@ -192,15 +187,15 @@ __global__ void __launch_bounds__(512) k_fft_y(cx<T>* __restrict__ data, int64_t
   C v[E];
 #pragma unroll
   for (int e = 0; e < E; e++) v[e] = base[(int64_t)(t + Tc * e) * NH];
-  fft_regs<C, E, kInterleaved>(v, sm, pf, t, c, TW, twf, dir);
+  fft_regs<C, E, kInterleaved, DIR>(v, sm, pf, t, c, TW, twf);
 #pragma unroll
   for (int e = 0; e < E; e++) base[(int64_t)(t + Tc * e) * NH] = v[e];
 }
 
 // ------------------------------------------------------------------ pass x (plain)
-template <typename T, int E>
-__global__ void __launch_bounds__(512) k_fft_x(const cx<T>* in, cx<T>* out, Geo g, FftPlan pf,
-                                               const cx<T>* __restrict__ twf, int TW, int dir) {
+template <typename T, int E, int DIR>
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_fft_x(const cx<T>* in, cx<T>* out, Geo g, FftPlan pf,
+                                                  const cx<T>* __restrict__ twf, int TW) {
   using C = cx<T>;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
@@ -213,7 +208,7 @@ __global__ void __launch_bounds__(512) k_fft_x(const cx<T>* in, cx<T>* out, Geo 
   C v[E];
 #pragma unroll
   for (int e = 0; e < E; e++) v[e] = in[off + (t + Tc * e) * si];
-  fft_regs<C, E, kInterleaved>(v, sm, pf, t, c, TW, twf, dir);
+  fft_regs<C, E, kInterleaved, DIR>(v, sm, pf, t, c, TW, twf);
 #pragma unroll
   for (int e = 0; e < E; e++) out[off + (t + Tc * e) * si] = v[e];
 }
@@ -223,7 +218,7 @@ __global__ void __launch_bounds__(512) k_fft_x(const cx<T>* in, cx<T>* out, Geo 
 // where some n_d = -N/2 when the inverse transform follows; stored as F0.
 // Binned: sum over modes of mult |X|^2 (slot SLOT_P0). Persistent over tiles.
 template <typename T, int E>
-__global__ void __launch_bounds__(512) k_combine_x(const cx<T>* B, cx<T>* F0, Geo g, FftPlan pf,
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_combine_x(const cx<T>* B, cx<T>* F0, Geo g, FftPlan pf,
                                                    const cx<T>* __restrict__ twf, int TW, int interlaced,
                                                    int compensate, int roundtrip, const cx<T>* __restrict__ phase,
                                                    const T* __restrict__ invw, BinArgs ba) {
@@ -248,7 +243,7 @@ __global__ void __launch_bounds__(512) k_combine_x(const cx<T>* B, cx<T>* F0, Ge
     C v[E];
 #pragma unroll
     for (int e = 0; e < E; e++) v[e] = B[off + (t + Tc * e) * si];
-    fft_regs<C, E, kInterleaved>(v, sm, pf, t, c, TW, twf, -1);
+    fft_regs<C, E, kInterleaved, -1>(v, sm, pf, t, c, TW, twf);
     const int ny = signed_freq(j, N);
     const C phy = ldg_c(phase + j), phz = ldg_c(phase + N + kz);
     const T wyz = invw[j] * invw[N + kz];
@@ -283,14 +278,13 @@ __global__ void __launch_bounds__(512) k_combine_x(const cx<T>* B, cx<T>* F0, Ge
 
 // ------------------------------------------------------------------ pass x + accumulate-and-bin
 // Per tile: F0 once (kept in shared memory, each thread its own modes); for each harmonic h
-// of the group, the x-pass of G_h (prefetched one harmonic ahead) and
-// acc += Y_{l,m(h)}(khat) Re[G_h conj(F0)] per mode; then mult * acc into the bins of `slot`.
+// of the group, the x-pass of G_h and acc += Y_{l,m(h)}(khat) Re[G_h conj(F0)] per mode;
+// then mult * acc into the bins of `slot`.
 template <typename T, int E>
-__global__ void __launch_bounds__(512) k_bin_x(const cx<T>* G, int64_t spec_stride, int ell, int h0, int M,
-                                               const cx<T>* __restrict__ F0, Geo g, FftPlan pf,
-                                               const cx<T>* __restrict__ twf, int TW, int slot, BinArgs ba) {
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_bin_x(const cx<T>* G, int64_t spec_stride, int ell, int h0, int M,
+                                                  const cx<T>* __restrict__ F0, Geo g, FftPlan pf,
+                                                  const cx<T>* __restrict__ twf, int TW, int slot, BinArgs ba) {
   using C = cx<T>;
-  constexpr bool kPrefetch = (E <= 8);
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = g.N, NH = g.NH, Tc = N / E;
   C* sm = reinterpret_cast<C*>(smraw);
@@ -302,6 +296,7 @@ __global__ void __launch_bounds__(512) k_bin_x(const cx<T>* G, int64_t spec_stri
   wb.w = reinterpret_cast<T*>(wb.b + ba.nk);
   wb.init();
   const YTab<T>& yt = ytab<T>();
+  const T sq2 = T(1.41421356237309504880);
   const int c = threadIdx.x % TW, t = threadIdx.x / TW;
   const int ntz = NH / TW, ntiles = N * ntz;
   const int64_t si = (int64_t)N * NH;
@@ -310,47 +305,46 @@ __global__ void __launch_bounds__(512) k_bin_x(const cx<T>* G, int64_t spec_stri
     const int j = tile / ntz, kz0 = (tile - j * ntz) * TW;
     const int kz = kz0 + c;
     const int64_t off = (int64_t)j * NH + kz;
-    const int ny = signed_freq(j, N);
+    const T fy = T(signed_freq(j, N)), fz = T(kz);
+    const T r2yz = fy * fy + fz * fz;
     T acc[E];
 #pragma unroll
     for (int e = 0; e < E; e++) {
       sF0[(t + Tc * e) * TW + c] = F0[off + (t + Tc * e) * si];
       acc[e] = T(0);
     }
-    C vn[E];
-    if (kPrefetch) {
-#pragma unroll
-      for (int e = 0; e < E; e++) vn[e] = G[off + (t + Tc * e) * si];
-    }
     for (int s = 0; s < M; s++) {
-      C v[E];
-      if (kPrefetch) {
-#pragma unroll
-        for (int e = 0; e < E; e++) v[e] = vn[e];
-        if (s + 1 < M) {
-          const C* Gn = G + (int64_t)(s + 1) * spec_stride;
-#pragma unroll
-          for (int e = 0; e < E; e++) vn[e] = Gn[off + (t + Tc * e) * si];
-        }
-      } else {
-        const C* Gs = G + (int64_t)s * spec_stride;
-#pragma unroll
-        for (int e = 0; e < E; e++) v[e] = Gs[off + (t + Tc * e) * si];
-      }
-      fft_regs<C, E, kInterleaved>(v, sm, pf, t, c, TW, twf, -1);
       const int h = h0 + s;
+      const int a = harm_a(h), sg = harm_sign(h);
+      const C* Gs = G + (int64_t)s * spec_stride;
+      C v[E];
+#pragma unroll
+      for (int e = 0; e < E; e++) v[e] = Gs[off + (t + Tc * e) * si];
+      fft_regs<C, E, kInterleaved, -1>(v, sm, pf, t, c, TW, twf);
 #pragma unroll
       for (int e = 0; e < E; e++) {
-        const int nx = signed_freq(t + Tc * e, N);
-        const int n2 = nx * nx + ny * ny + kz * kz;
-        if (n2 == 0) continue;
-        const T Y = ylm_dir<T>(yt, ell, h, T(nx), T(ny), T(kz), T(n2));
+        const T fx = T(signed_freq(t + Tc * e, N));
+        const T r2 = fx * fx + r2yz;
+        if (r2 == T(0)) continue;
+        const T inv = rsqrt_t<T>(r2);
+        const T x = fx * inv, y = fy * inv;
+        T Y = ylm_q<T>(yt, ell, a, fz * inv);
+        if (a > 0) {
+          T pr = x, pi = y;
+          for (int u = 1; u < a; u++) {
+            const T nr = pr * x - pi * y;
+            pi = pr * y + pi * x;
+            pr = nr;
+          }
+          Y = sq2 * Y * (sg > 0 ? pr : pi);
+        }
         const C fv = sF0[(t + Tc * e) * TW + c];
         acc[e] += Y * (v[e].x * fv.x + v[e].y * fv.y);
       }
     }
     if (j != N / 2) {
       const T mult = kz ? T(2) : T(1);
+      const int ny = signed_freq(j, N);
 #pragma unroll
       for (int e = 0; e < E; e++) {
         const int ii = t + Tc * e;
@@ -444,20 +438,25 @@ void launch_c2r_z(const cx<T>* in, T* out, const Geo& g, const FftPlan& pz, int 
 }
 
 template <typename T> size_t smem_ylm_z(const Geo& g, int E, int M, int rows, int threads) {
-  const int spr = threads / (g.NH / E);
-  return (size_t)M * rows * g.N * sizeof(T) + smem_rows(g.NH, spr, sizeof(cx<T>));
+  (void)E;
+  (void)threads;
+  const size_t stage = (size_t)M * rows * g.N * sizeof(T);
+  const size_t xb = smem_rows(g.NH, M * rows, sizeof(cx<T>));
+  return stage > xb ? stage : xb;
 }
 
 template <typename T>
 void launch_ylm_r2c_z(const T* f, cx<T>* out, int64_t spec_stride, int ell, int h0, int M, const Geo& g,
                       const FftPlan& pz, int E, const cx<T>* tw_half, const cx<T>* twr, const T* axis_pos, int rows,
                       int threads, cudaStream_t s) {
-  const size_t smem = smem_ylm_z<T>(g, E, M, rows, threads);
+  (void)threads;
+  const size_t smem = smem_ylm_z<T>(g, E, M, rows, 0);
+  const int nthreads = M * rows * (g.NH / E);
   const unsigned grid = (unsigned)((int64_t)g.N * g.N / rows);
   PSPEC_DISPATCH_E(E, {
     set_smem(k_ylm_r2c_z<T, EE>, smem);
-    k_ylm_r2c_z<T, EE><<<grid, threads, smem, s>>>(f, out, spec_stride, ell, h0, M, g, pz, tw_half, twr, axis_pos,
-                                                   rows);
+    k_ylm_r2c_z<T, EE><<<grid, nthreads, smem, s>>>(f, out, spec_stride, ell, h0, M, g, pz, tw_half, twr, axis_pos,
+                                                    rows);
   });
 }
 
@@ -470,8 +469,13 @@ void launch_fft_y(cx<T>* data, int64_t spec_stride, int nspec, const Geo& g, con
   dim3 grid((unsigned)(g.N * (g.NH / tw)), (unsigned)nspec);
   const int threads = tw * (g.N / E);
   PSPEC_DISPATCH_E(E, {
-    set_smem(k_fft_y<T, EE>, smem);
-    k_fft_y<T, EE><<<grid, threads, smem, s>>>(data, spec_stride, g, pf, tw_full, tw, dir);
+    if (dir < 0) {
+      set_smem(k_fft_y<T, EE, -1>, smem);
+      k_fft_y<T, EE, -1><<<grid, threads, smem, s>>>(data, spec_stride, g, pf, tw_full, tw);
+    } else {
+      set_smem(k_fft_y<T, EE, 1>, smem);
+      k_fft_y<T, EE, 1><<<grid, threads, smem, s>>>(data, spec_stride, g, pf, tw_full, tw);
+    }
   });
 }
 
@@ -480,9 +484,15 @@ void launch_fft_x(const cx<T>* in, cx<T>* out, const Geo& g, const FftPlan& pf, 
                   int dir, cudaStream_t s) {
   const size_t smem = smem_cols<T>(g, tw);
   const int threads = tw * (g.N / E);
+  const unsigned grid = (unsigned)(g.N * (g.NH / tw));
   PSPEC_DISPATCH_E(E, {
-    set_smem(k_fft_x<T, EE>, smem);
-    k_fft_x<T, EE><<<(unsigned)(g.N * (g.NH / tw)), threads, smem, s>>>(in, out, g, pf, tw_full, tw, dir);
+    if (dir < 0) {
+      set_smem(k_fft_x<T, EE, -1>, smem);
+      k_fft_x<T, EE, -1><<<grid, threads, smem, s>>>(in, out, g, pf, tw_full, tw);
+    } else {
+      set_smem(k_fft_x<T, EE, 1>, smem);
+      k_fft_x<T, EE, 1><<<grid, threads, smem, s>>>(in, out, g, pf, tw_full, tw);
+    }
   });
 }
 

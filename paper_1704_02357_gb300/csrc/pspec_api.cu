@@ -17,7 +17,7 @@ constexpr size_t kAlign = 256;
 constexpr size_t kSmemBudget = 200 * 1024;   // one block
 constexpr size_t kSmemShared = 100 * 1024;   // two blocks per SM
 constexpr int kMaxElls = PSPEC_MAX_ELL / 2 + 1;
-constexpr int kYlmThreads = 256;
+constexpr int kYlmMaxThreads = 512;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -135,13 +135,10 @@ pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl,
   while (pl->rows_z > 1 && (((int64_t)N * N) % pl->rows_z || smem_rows(NH, pl->rows_z, csz) > kSmemShared))
     pl->rows_z >>= 1;
 
-  // harmonics per group: staging of M rows of N reals + the exchange buffer
+  // harmonics per group (spectra buffered between the z and x passes): bounded by memory
   const int nharm = 2 * p->ell_max + 1;
-  const int spr = kYlmThreads / Tz;
-  const size_t xb = smem_rows(NH, spr, csz);
-  int m_smem = (int)((kSmemBudget - xb) / ((size_t)N * pl->esz));
   int m_mem = p->max_group_bytes > 0 ? (int)(p->max_group_bytes / (int64_t)pl->Sc) : nharm;
-  pl->group_max = p->ell_max == 0 ? 0 : std::max(1, std::min(nharm, std::min(m_smem, m_mem)));
+  pl->group_max = p->ell_max == 0 ? 0 : std::max(1, std::min(nharm, m_mem));
 
   if (f64) {
     pl->ctas_comb = persistent_ctas<double>(0, pl->g, pl->E, pl->tw_comb, max_kbins, nsm);
@@ -498,14 +495,20 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
     const int nh = 2 * ell + 1;
     for (int h0 = 0; h0 < nh; h0 += pl.group_max) {
       const int M = std::min(pl.group_max, nh - h0);
-      int rows = std::max(1, pow2_floor(std::max(1, 96 * 1024 / (M * N * pl.esz))));
-      while (rows > 1 && (((int64_t)N * N) % rows ||
-                          (pl.esz == 4 ? smem_ylm_z<float>(g, E, M, rows, kYlmThreads)
-                                       : smem_ylm_z<double>(g, E, M, rows, kYlmThreads)) > kSmemBudget))
-        rows >>= 1;
-      TRY(run(c, PSPEC_K_YLM_Z, acc(Sr + M * Sc), [&] {
-        launch_ylm_r2c_z<T>(f, G, stride, ell, h0, M, g, pl.pz, E, twh, twr, axis, rows, kYlmThreads, s);
-      }));
+      // z pass with the Y_lm weights: one block holds Ms harmonics x rows rows, Tz threads each
+      const int Tz = g.NH / E;
+      const int ms_max = std::max(1, kYlmMaxThreads / Tz);
+      for (int hs = 0; hs < M; hs += ms_max) {
+        const int Ms = std::min(ms_max, M - hs);
+        int rows = std::max(1, pow2_floor(std::max(1, kYlmMaxThreads / (Ms * Tz))));
+        while (rows > 1 && (((int64_t)N * N) % rows ||
+                            (pl.esz == 4 ? smem_ylm_z<float>(g, E, Ms, rows, 0)
+                                         : smem_ylm_z<double>(g, E, Ms, rows, 0)) > kSmemBudget))
+          rows >>= 1;
+        TRY(run(c, PSPEC_K_YLM_Z, acc(Sr + Ms * Sc), [&] {
+          launch_ylm_r2c_z<T>(f, G + hs * stride, stride, ell, h0 + hs, Ms, g, pl.pz, E, twh, twr, axis, rows, 0, s);
+        }));
+      }
       TRY(run(c, PSPEC_K_FFT_Y, acc(2 * M * Sc), [&] { launch_fft_y<T>(G, stride, M, g, pl.pf, E, twf, pl.tw_y, -1, s); }));
       TRY(run(c, PSPEC_K_BIN_X, acc(Sc + M * Sc), [&] {
         launch_bin_x<T>(G, stride, ell, h0, M, F0, g, pl.pf, E, twf, pl.tw_bin, SLOT_ELL0 + i, ba, pl.ctas_bin, s);
