@@ -138,6 +138,25 @@ pspec_status pspec_multipoles_device(void* ctx, const int32_t* ells, int32_t n_e
 pspec_status pspec_wedges(const double* P, const int32_t* ells, int32_t n_ells, int32_t n_kbins,
                           const double* mu_edges, int32_t n_mu, double* out, void* stream);
 
+/* Catalog sums without any device allocation. The paper has no counterpart: this exists
+ * for callers that cannot call cudaMalloc (code that runs while a CUDA graph is being
+ * captured, runtimes without a device allocator, or frameworks whose memory pool owns every
+ * byte of the device). It computes what pspec_paint computes for alpha, I and S, into the
+ * caller's DEVICE buffer `out` of 10 doubles: [0] W_d, [1] W_r, [2] alpha, [3] I, [4] S,
+ * [5] 0, [6] 0, [7] sum_data v^2, [8] sum_randoms v^2, [9] sum_randoms nbar w_c w_fkp^2,
+ * for the box, n̄ and P0 of `p` (the rest of `p` is not used). Invalid particles are left out.
+ * Scratch: a fixed 64 KiB device array inside the library, held by every GPU that loads it
+ * until the process exits; `nblocks` partial sums per catalog (0 = twice the SM count, at
+ * most PSPEC_NOALLOC_MAX_BLOCKS; a larger value gives PSPEC_EINVAL). The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture. Every call on a device shares
+ * the array, so calls that overlap on the GPU (different streams, no ordering) race. The
+ * call is enqueued on `stream` and does not synchronise. */
+#define PSPEC_NOALLOC_MAX_BLOCKS 1024
+pspec_status pspec_catalog_sums_noalloc(const pspec_params* p, const pspec_catalog* data,
+                                        const pspec_catalog* randoms, int32_t nblocks, double* out,
+                                        void* stream);
+
 /* Plan facts for tests and reports. */
 typedef struct {
   int32_t nmesh, precision, ell_max;

@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpspec.so")
-SOURCES = ["k_fft.cu", "k_misc.cu", "pspec_api.cu"]
+SOURCES = ["k_fft.cu", "k_misc.cu", "pspec_api.cu", "noalloc.cu"]
 HEADERS = ["common.cuh", "fft_engine.cuh", "launch.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -78,6 +78,8 @@ SIGNATURES = [
     ("pspec_strerror", C.c_char_p, [C.c_int32]),
     ("pspec_last_error", C.c_char_p, [C.c_void_p]),
     ("pspec_version", C.c_char_p, []),
+    ("pspec_catalog_sums_noalloc", C.c_int32, [C.POINTER(Params), C.POINTER(Catalog), C.POINTER(Catalog), C.c_int32,
+                                               C.c_void_p, C.c_void_p]),
 ]
 
 
@@ -247,3 +249,18 @@ def wedges(P, ells: Sequence[int], mu_edges, stream=None):
                             mu.ctypes.data_as(C.POINTER(C.c_double)), n_mu, C.c_void_p(out.data_ptr()),
                             C.c_void_p(s.cuda_stream)))
     return out
+
+
+def catalog_sums_noalloc(params: Params, data_pos, randoms_pos, out, data_weight=None, data_nbar=None,
+                         randoms_weight=None, randoms_nbar=None, nblocks=0, stream=None):
+    """Enqueue pspec_catalog_sums_noalloc: `out` is a float64 CUDA tensor of >= 10 elements."""
+    import torch
+    lib = load()
+    keep = []
+    d = _catalog(data_pos, data_weight, data_nbar, out.device, keep)
+    r = _catalog(randoms_pos, randoms_weight, randoms_nbar, out.device, keep)
+    s = stream if stream is not None else torch.cuda.current_stream(out.device)
+    st = lib.pspec_catalog_sums_noalloc(C.byref(params), C.byref(d), C.byref(r), int(nblocks),
+                                        C.c_void_p(out.data_ptr()), C.c_void_p(s.cuda_stream))
+    _check(st)
+    return keep
