@@ -16,8 +16,9 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpspec.so")
-SOURCES = ["k_fft.cu", "k_misc.cu", "pspec_api.cu", "noalloc.cu"]
-HEADERS = ["common.cuh", "fft_engine.cuh", "launch.h"]
+SOURCES = ["k_fft.cu", "k_misc.cu", "pspec_api.cu", "noalloc.cu", "pass_small.cu", "pass_256.cu", "pass_512.cu",
+           "pass_1024.cu", "pass_3small.cu", "pass_384.cu", "pass_768.cu"]
+HEADERS = ["common.cuh", "fft_engine.cuh", "launch.h", "k_fft_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -61,7 +62,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stderr.write(r.stderr)
         return obj
 
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    with ThreadPoolExecutor(max_workers=min(len(SOURCES), max(2, os.cpu_count() or 2))) as ex:
         objs = list(ex.map(one, SOURCES))
     tmp = LIB + ".tmp"
     cmd = [cc, "-shared", "-o", tmp] + objs + ARCH

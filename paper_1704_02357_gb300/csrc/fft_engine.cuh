@@ -1,118 +1,161 @@
-// Register-resident Stockham FFT engine for the transform passes.
+// Register-resident Stockham FFT engine for the transform passes, with the transform length
+// and the tile shape fixed at compile time.
 //
 // A sequence of length L is spread over Tc = L/E threads; thread t of a sequence holds the
 // E elements t + Tc*e (e = 0..E-1) in registers. Every stage reads exactly that set (a
 // radix-R butterfly q uses slots q + r*E/R), so the first stage is fed straight from
 // global memory and the last stage's outputs land back in the same slots in natural
 // order, ready to be stored. Between stages the butterfly outputs go through shared
-// memory: L/E-stage transforms cost (stages - 1) shared-memory exchanges.
+// memory: an S-stage transform costs S - 1 shared-memory exchanges.
 //
 // Stage with radix R after Ns = product of earlier radices: butterfly j (k = j mod Ns)
 // twiddles input r by w_L^{r k L/(Ns R)}, takes an R-point DFT and writes output r to
-// position (j - k) R + k + r Ns. Radix 3, when present, is the last stage, so every Ns
-// before it is a power of two and k = j mod Ns is a mask; in the last stage k = j.
+// position (j - k) R + k + r Ns. Radices are 8, 4, 2 (largest first) and a factor 3 last,
+// so every Ns before the last stage is a power of two and k = j mod Ns is a mask; in the
+// last stage k = j.
 #pragma once
+#include <type_traits>
 #include "common.cuh"
 
 namespace pspec {
 
+// ------------------------------------------------------------------ compile-time plans
+constexpr int elems_for(int N) { return N % 3 == 0 ? 24 : 8; }
+
+struct CtPlan {
+  int nst;
+  int rad[12];
+  int ns[12];
+};
+
+__host__ __device__ constexpr CtPlan ct_plan(int L) {
+  CtPlan p{0, {0}, {0}};
+  int x = L, ns = 1, three = 0;
+  while (x % 3 == 0) {
+    x /= 3;
+    three++;
+  }
+  while (x % 8 == 0) {
+    p.rad[p.nst] = 8;
+    p.ns[p.nst] = ns;
+    ns *= 8;
+    x /= 8;
+    p.nst++;
+  }
+  while (x % 4 == 0) {
+    p.rad[p.nst] = 4;
+    p.ns[p.nst] = ns;
+    ns *= 4;
+    x /= 4;
+    p.nst++;
+  }
+  while (x % 2 == 0) {
+    p.rad[p.nst] = 2;
+    p.ns[p.nst] = ns;
+    ns *= 2;
+    x /= 2;
+    p.nst++;
+  }
+  for (int i = 0; i < three; i++) {
+    p.rad[p.nst] = 3;
+    p.ns[p.nst] = ns;
+    ns *= 3;
+    p.nst++;
+  }
+  return p;
+}
+
+template <int B, int E, typename F> __device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (B < E) {
+    f(std::integral_constant<int, B>{});
+    static_for<B + 1, E>(f);
+  }
+}
+
 // Shared-memory layouts of the exchange buffer.
-//   kInterleaved: [pos][nseq], sequence fastest (columns of a tile; lanes run across seqs)
+//   kInterleaved: [pos][NSEQ], sequence fastest (columns of a tile; lanes run across seqs)
 //   kPaddedRows:  [seq][L + L/16], position fastest with one pad slot per 16 (rows)
 enum { kInterleaved = 0, kPaddedRows = 1 };
 
-template <int LAYOUT>
-__device__ __forceinline__ int sidx(int seq, int pos, int nseq, int Lp) {
-  return LAYOUT == kInterleaved ? pos * nseq + seq : seq * Lp + pos + (pos >> 4);
-}
+__host__ __device__ constexpr int padded_len(int L) { return L + (L >> 4); }
 
-__host__ __device__ __forceinline__ int padded_len(int L) { return L + (L >> 4); }
+template <int LAYOUT, int L, int NSEQ>
+__device__ __forceinline__ int sidx(int seq, int pos) {
+  if constexpr (LAYOUT == kInterleaved)
+    return pos * NSEQ + seq;
+  else
+    return seq * padded_len(L) + pos + (pos >> 4);
+}
 
 template <typename C> __device__ __forceinline__ C ldg_c(const C* p) { return __ldg(p); }
 
-template <typename C, int E, int R, int LAYOUT, int DIR>
-__device__ __forceinline__ void stage_regs(C (&v)[E], C* sm, int t, int Tc, int L, int Ns, bool last, int seq,
-                                           int nseq, int Lp, const C* __restrict__ tw) {
+template <typename C, int E, int L, int R, int NS, bool LAST, int LAYOUT, int NSEQ, int DIR>
+__device__ __forceinline__ void stage_ct(C (&v)[E], C* sm, int t, int seq, const C* __restrict__ tw) {
   constexpr int Q = E / R;
-  const int tstep = L / (Ns * R);
-  // When Ns divides Tc (both powers of two) every butterfly of this thread has the same
-  // k = t mod Ns, so with several butterflies (Q > 1) its R - 1 twiddles are loaded once.
-  const bool shared_k = (Q > 1) && (Ns > 1) && !last && (Ns <= Tc);
-  C ws[R > 1 && Q > 1 ? R : 1];
-  if constexpr (Q > 1) if (shared_k) {
-    const int k = t & (Ns - 1);
+  constexpr int Tc = L / E;
+  constexpr int TSTEP = L / (NS * R);
+  // With NS | Tc every butterfly of this thread has k = t mod NS: load its twiddles once.
+  constexpr bool kShared = (Q > 1) && (NS > 1) && !LAST && (NS <= Tc);
+  C ws[kShared ? R : 1];
+  if constexpr (kShared) {
+    const int k = t & (NS - 1);
 #pragma unroll
     for (int r = 1; r < R; r++) {
-      ws[r] = ldg_c(tw + r * k * tstep);
+      ws[r] = ldg_c(tw + r * k * TSTEP);
       if (DIR > 0) ws[r].y = -ws[r].y;
     }
   }
 #pragma unroll
   for (int q = 0; q < Q; q++) {
     const int j = t + Tc * q;
-    const int k = last ? j : (j & (Ns - 1));
+    const int k = LAST ? j : (j & (NS - 1));
     C u[R];
 #pragma unroll
     for (int r = 0; r < R; r++) u[r] = v[q + r * Q];
-    if constexpr (Q > 1) {
-      if (shared_k) {
-#pragma unroll
-        for (int r = 1; r < R; r++) u[r] = cmul(u[r], ws[r]);
-      }
-    }
-    if (!shared_k && Ns > 1) {
+    if constexpr (NS > 1) {
 #pragma unroll
       for (int r = 1; r < R; r++) {
-        C w = ldg_c(tw + r * k * tstep);
-        if (DIR > 0) w.y = -w.y;
+        C w;
+        if constexpr (kShared) {
+          w = ws[r];
+        } else {
+          w = ldg_c(tw + r * k * TSTEP);
+          if (DIR > 0) w.y = -w.y;
+        }
         u[r] = cmul(u[r], w);
       }
     }
     Dft<C, R>::run(u, DIR);
-    if (last) {
+    if constexpr (LAST) {
 #pragma unroll
       for (int r = 0; r < R; r++) v[q + r * Q] = u[r];
     } else {
       const int base = (j - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; r++) sm[sidx<LAYOUT>(seq, base + r * Ns, nseq, Lp)] = u[r];
+      for (int r = 0; r < R; r++) sm[sidx<LAYOUT, L, NSEQ>(seq, base + r * NS)] = u[r];
     }
   }
 }
 
-// Transforms the sequence whose slots this thread holds (DIR = -1 forward, +1 inverse).
-// All threads of the block must call it (it contains __syncthreads); the shared buffer is
-// free again when it returns.
-template <typename C, int E, int LAYOUT, int DIR>
-__device__ __forceinline__ void fft_regs(C (&v)[E], C* sm, const FftPlan& p, int t, int seq, int nseq,
-                                         const C* __restrict__ tw) {
-  const int L = p.L;
-  const int Tc = L / E;
-  const int Lp = padded_len(L);
-  for (int s = 0; s < p.nst; s++) {
-    const bool last = (s == p.nst - 1);
-    const int Ns = p.ns[s];
-    switch (p.rad[s]) {
-      case 8:
-        if constexpr (E % 8 == 0) stage_regs<C, E, 8, LAYOUT, DIR>(v, sm, t, Tc, L, Ns, last, seq, nseq, Lp, tw);
-        break;
-      case 4:
-        if constexpr (E % 4 == 0) stage_regs<C, E, 4, LAYOUT, DIR>(v, sm, t, Tc, L, Ns, last, seq, nseq, Lp, tw);
-        break;
-      case 3:
-        if constexpr (E % 3 == 0) stage_regs<C, E, 3, LAYOUT, DIR>(v, sm, t, Tc, L, Ns, last, seq, nseq, Lp, tw);
-        break;
-      default:
-        if constexpr (E % 2 == 0) stage_regs<C, E, 2, LAYOUT, DIR>(v, sm, t, Tc, L, Ns, last, seq, nseq, Lp, tw);
-        break;
-    }
-    if (!last) {
+// Transforms the length-L sequence whose slots this thread holds (DIR = -1 forward, +1
+// inverse). All threads of the block must call it (it contains __syncthreads); the shared
+// buffer is free again when it returns. NSEQ is the number of interleaved sequences
+// (kInterleaved only).
+template <typename C, int E, int L, int LAYOUT, int NSEQ, int DIR>
+__device__ __forceinline__ void fft_ct(C (&v)[E], C* sm, int t, int seq, const C* __restrict__ tw) {
+  constexpr CtPlan P = ct_plan(L);
+  constexpr int Tc = L / E;
+  static_for<0, P.nst>([&](auto s_) {
+    constexpr int s = decltype(s_)::value;
+    constexpr bool last = (s == P.nst - 1);
+    stage_ct<C, E, L, P.rad[s], P.ns[s], last, LAYOUT, NSEQ, DIR>(v, sm, t, seq, tw);
+    if constexpr (!last) {
       __syncthreads();
 #pragma unroll
-      for (int e = 0; e < E; e++) v[e] = sm[sidx<LAYOUT>(seq, t + Tc * e, nseq, Lp)];
+      for (int e = 0; e < E; e++) v[e] = sm[sidx<LAYOUT, L, NSEQ>(seq, t + Tc * e)];
       __syncthreads();
     }
-  }
+  });
 }
 
 // Per-warp histograms flushed into per-block FP64 bins. On the FP32 path the warp partials

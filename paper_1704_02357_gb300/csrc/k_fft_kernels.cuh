@@ -1,0 +1,498 @@
+// Transform passes of the SH-FFT multipole estimator (Sec. 2.1 eqs. Pell-ours, Fell;
+// Sec. 2.3 interlacing, compensation and the inverse transform before the Y_lm weights),
+// as templates on the mesh side N; each supported N is instantiated in its own translation
+// unit (pass_<N>.cu) and reached through a PassTable.
+//
+// Storage: real mesh r[(i*N + j)*N + k]; half spectrum s[(i*N + j)*NH + kz], NH = N/2.
+// The kz = N/2 plane is never stored: its modes are zeroed before the inverse transform
+// and never binned, so nothing downstream reads it.
+//
+// A 3-D forward transform is three passes, each one HBM round trip:
+//   z: rows of N reals -> N/2-point complex FFT of packed pairs -> unpack to N/2 modes
+//   y: columns along j of an (i, kz-tile) slab, in place
+//   x: columns along i of a (j, kz-tile) slab; fused with the interlace/compensate
+//      combine (F0 and the l = 0 sums) or with the Y_lm(khat) accumulate-and-bin.
+// Every pass keeps its elements in registers (fft_engine.cuh); kz tiles of TW columns give
+// TW*8-byte contiguous segments per row.
+#pragma once
+#include <cmath>
+#include "launch.h"
+#include "fft_engine.cuh"
+
+namespace pspec {
+
+// ------------------------------------------------------------------ compile-time shapes
+template <int N> struct Shape {
+  static constexpr int NH = N / 2;
+  static constexpr int E = elems_for(N);
+  static constexpr int Tz = NH / E;      // threads per row in the z passes
+  static constexpr int Tc = N / E;       // threads per column in the y / x passes
+  static constexpr int TW = col_tile(N); // kz columns per tile
+  static constexpr int ROWS = z_rows(N); // rows per block in the plain z passes
+  static constexpr int CT = TW * Tc;     // threads of a column block
+  static constexpr int ZT = ROWS * Tz;   // threads of a row block
+};
+
+template <typename T> constexpr int min_blocks(int threads) {
+  return sizeof(T) == 4 ? (threads >= 512 ? 2 : (threads >= 256 ? 3 : 4)) : 1;
+}
+
+template <int N> __device__ __forceinline__ int sfreq(int i) { return i < N / 2 ? i : i - N; }
+
+// r2c unpack: X[k] = (Z[k] + Z*[L-k])/2 - i/2 w^k (Z[k] - Z*[L-k]), w = exp(-2 pi i/N)
+template <typename C, typename T>
+__device__ __forceinline__ C r2c_unpack(C zk, C zm, C w) {
+  const C zc = cconj(zm);
+  const C e = cscale(cadd(zk, zc), T(0.5));
+  const C d = csub(zk, zc);
+  const C o = mk(T(0.5) * d.y, T(-0.5) * d.x);
+  return cadd(e, cmul(w, o));
+}
+
+// ------------------------------------------------------------------ pass z: r2c of plain rows
+template <typename T, int N>
+__global__ void __launch_bounds__(Shape<N>::ZT, min_blocks<T>(Shape<N>::ZT))
+    k_r2c_z(const T* __restrict__ in, cx<T>* __restrict__ out, const cx<T>* __restrict__ twh,
+            const cx<T>* __restrict__ twr) {
+  using C = cx<T>;
+  using S = Shape<N>;
+  constexpr int L = S::NH, E = S::E, Tc = S::Tz;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  const int r = threadIdx.x / Tc, t = threadIdx.x - r * Tc;
+  const int row = blockIdx.x * S::ROWS + r;
+  const C* src = reinterpret_cast<const C*>(in + (int64_t)row * N);
+  C v[E];
+#pragma unroll
+  for (int e = 0; e < E; e++) v[e] = src[t + Tc * e];
+  fft_ct<C, E, L, kPaddedRows, 1, -1>(v, sm, t, r, twh);
+#pragma unroll
+  for (int e = 0; e < E; e++) sm[sidx<kPaddedRows, L, 1>(r, t + Tc * e)] = v[e];
+  __syncthreads();
+  C* dst = out + (int64_t)row * L;
+#pragma unroll
+  for (int e = 0; e < E; e++) {
+    const int k = t + Tc * e;
+    const C zm = sm[sidx<kPaddedRows, L, 1>(r, k ? L - k : 0)];
+    dst[k] = r2c_unpack<C, T>(v[e], zm, ldg_c(twr + k));
+  }
+}
+
+// ------------------------------------------------------------------ pass z: c2r
+// Rows of L stored modes (the kz = N/2 mode taken as 0) -> N reals, times `scale`.
+template <typename T, int N>
+__global__ void __launch_bounds__(Shape<N>::ZT, min_blocks<T>(Shape<N>::ZT))
+    k_c2r_z(const cx<T>* __restrict__ in, T* __restrict__ out, const cx<T>* __restrict__ twh,
+            const cx<T>* __restrict__ twr, T scale) {
+  using C = cx<T>;
+  using S = Shape<N>;
+  constexpr int L = S::NH, E = S::E, Tc = S::Tz;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  const int r = threadIdx.x / Tc, t = threadIdx.x - r * Tc;
+  const int row = blockIdx.x * S::ROWS + r;
+  const C* src = in + (int64_t)row * L;
+  C v[E];
+#pragma unroll
+  for (int e = 0; e < E; e++) {
+    const int k = t + Tc * e;
+    const C xk = src[k];
+    const C xm = k ? cconj(src[L - k]) : mk(T(0), T(0));
+    const C ev = cscale(cadd(xk, xm), T(0.5));
+    const C od = cmul(cscale(csub(xk, xm), T(0.5)), cconj(ldg_c(twr + k)));
+    v[e] = mk(ev.x - od.y, ev.y + od.x);  // E + i O
+  }
+  fft_ct<C, E, L, kPaddedRows, 1, +1>(v, sm, t, r, twh);
+  C* dst = reinterpret_cast<C*>(out + (int64_t)row * N);
+#pragma unroll
+  for (int e = 0; e < E; e++) dst[t + Tc * e] = cscale(v[e], scale);
+}
+
+// ------------------------------------------------------------------ pass z: Y_lm-weighted r2c
+// For `rows` rows of f and the M harmonics h0..h0+M-1 of multipole l. Every point sweeps
+// its harmonics once ((x+iy)^a carried from one |m| to the next) into a shared staging
+// area of nseq = M*rows real rows; then each of the nseq*Tz threads loads its slots, the
+// sequences are transformed (the staging area is reused as the exchange buffer) and
+// unpacked into the M spectra.
+template <typename T, int N>
+__global__ void __launch_bounds__(512) k_ylm_r2c_z(const T* __restrict__ f, cx<T>* __restrict__ out,
+                                                  int64_t spec_stride, int ell, int h0, int M,
+                                                  const cx<T>* __restrict__ twh, const cx<T>* __restrict__ twr,
+                                                  const T* __restrict__ axis, int rows,
+                                                  const __grid_constant__ YTab<T> yt) {
+  using C = cx<T>;
+  using S = Shape<N>;
+  constexpr int L = S::NH, E = S::E, Tc = S::Tz;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* stage = reinterpret_cast<T*>(smraw);  // [nseq][N] reals, then the exchange buffer
+  C* xb = reinterpret_cast<C*>(smraw);
+  const int row0 = blockIdx.x * rows;
+  const int a_lo = harm_a(h0), a_hi = harm_a(h0 + M - 1);
+  const T sq2 = T(1.41421356237309504880);
+  for (int r = 0; r < rows; r++) {
+    const int grow = row0 + r;
+    const int i = grow / N, j = grow - i * N;
+    const T vx = axis[i], vy = axis[N + j];
+    const T* frow = f + (int64_t)grow * N;
+    for (int kk = threadIdx.x; kk < N; kk += blockDim.x) {
+      const T fv = frow[kk];
+      const T vz = axis[2 * N + kk];
+      const T r2 = vx * vx + vy * vy + vz * vz;
+      if (r2 == T(0)) {
+        for (int s = 0; s < M; s++) stage[(s * rows + r) * N + kk] = T(0);
+        continue;
+      }
+      const T inv = rsqrt_t<T>(r2);
+      const T x = vx * inv, y = vy * inv, z = vz * inv;
+      T pr = T(1), pi = T(0);
+      for (int s = 0; s < a_lo; s++) {
+        const T nr = pr * x - pi * y;
+        pi = pr * y + pi * x;
+        pr = nr;
+      }
+      for (int a = a_lo; a <= a_hi; a++) {
+        const T q = fv * ylm_q<T>(yt, ell, a, z);
+        if (a == 0) {
+          stage[r * N + kk] = q;
+        } else {
+          const int hp = 2 * a - 1, hm = 2 * a;
+          if (hp >= h0 && hp < h0 + M) stage[((hp - h0) * rows + r) * N + kk] = sq2 * q * pr;
+          if (hm >= h0 && hm < h0 + M) stage[((hm - h0) * rows + r) * N + kk] = sq2 * q * pi;
+        }
+        const T nr = pr * x - pi * y;
+        pi = pr * y + pi * x;
+        pr = nr;
+      }
+    }
+  }
+  __syncthreads();
+  const C* stc = reinterpret_cast<const C*>(stage);
+  const int sq = threadIdx.x / Tc, t = threadIdx.x - sq * Tc;
+  C v[E];
+#pragma unroll
+  for (int e = 0; e < E; e++) v[e] = stc[sq * L + t + Tc * e];
+  __syncthreads();
+  fft_ct<C, E, L, kPaddedRows, 1, -1>(v, xb, t, sq, twh);
+#pragma unroll
+  for (int e = 0; e < E; e++) xb[sidx<kPaddedRows, L, 1>(sq, t + Tc * e)] = v[e];
+  __syncthreads();
+  const int s = sq / rows, r = sq - s * rows;
+  C* dst = out + s * spec_stride + (int64_t)(row0 + r) * L;
+#pragma unroll
+  for (int e = 0; e < E; e++) {
+    const int k = t + Tc * e;
+    const C zm = xb[sidx<kPaddedRows, L, 1>(sq, k ? L - k : 0)];
+    dst[k] = r2c_unpack<C, T>(v[e], zm, ldg_c(twr + k));
+  }
+}
+
+// ------------------------------------------------------------------ pass y (in place)
+// Block: one (i, kz-tile) slab, TW columns x Tc threads (column fastest).
+template <typename T, int N, int DIR>
+__global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T>(Shape<N>::CT))
+    k_fft_y(cx<T>* __restrict__ data, int64_t spec_stride, const cx<T>* __restrict__ twf) {
+  using C = cx<T>;
+  using S = Shape<N>;
+  constexpr int NH = S::NH, E = S::E, Tc = S::Tc, TW = S::TW;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  const int c = threadIdx.x % TW, t = threadIdx.x / TW;
+  constexpr int ntz = NH / TW;
+  const int i = blockIdx.x / ntz, kz0 = (blockIdx.x - i * ntz) * TW;
+  C* base = data + (int64_t)blockIdx.y * spec_stride + (int64_t)i * N * NH + kz0 + c;
+  C v[E];
+#pragma unroll
+  for (int e = 0; e < E; e++) v[e] = base[(int64_t)(t + Tc * e) * NH];
+  fft_ct<C, E, N, kInterleaved, TW, DIR>(v, sm, t, c, twf);
+#pragma unroll
+  for (int e = 0; e < E; e++) base[(int64_t)(t + Tc * e) * NH] = v[e];
+}
+
+// ------------------------------------------------------------------ pass x (plain)
+template <typename T, int N, int DIR>
+__global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T>(Shape<N>::CT))
+    k_fft_x(const cx<T>* in, cx<T>* out, const cx<T>* __restrict__ twf) {
+  using C = cx<T>;
+  using S = Shape<N>;
+  constexpr int NH = S::NH, E = S::E, Tc = S::Tc, TW = S::TW;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  const int c = threadIdx.x % TW, t = threadIdx.x / TW;
+  constexpr int ntz = NH / TW;
+  const int j = blockIdx.x / ntz, kz0 = (blockIdx.x - j * ntz) * TW;
+  constexpr int64_t si = (int64_t)N * NH;
+  const int64_t off = (int64_t)j * NH + kz0 + c;
+  C v[E];
+#pragma unroll
+  for (int e = 0; e < E; e++) v[e] = in[off + (t + Tc * e) * si];
+  fft_ct<C, E, N, kInterleaved, TW, DIR>(v, sm, t, c, twf);
+#pragma unroll
+  for (int e = 0; e < E; e++) out[off + (t + Tc * e) * si] = v[e];
+}
+
+// ------------------------------------------------------------------ pass x + combine (F0) + l = 0 sums
+// X = (F1 + exp(-i k.s) F2)/2 (interlaced) or F1; divided by W(k) when compensating; zeroed
+// where some n_d = -N/2 when the inverse transform follows; stored as F0.
+// Binned: sum over modes of mult |X|^2 (slot SLOT_P0). Persistent over tiles.
+template <typename T, int N>
+__global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T>(Shape<N>::CT))
+    k_combine_x(const cx<T>* B, cx<T>* F0, const cx<T>* __restrict__ twf, int interlaced, int compensate,
+                int roundtrip, const cx<T>* __restrict__ phase, const T* __restrict__ invw, BinArgs ba) {
+  using C = cx<T>;
+  using S = Shape<N>;
+  constexpr int NH = S::NH, E = S::E, Tc = S::Tc, TW = S::TW;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  WarpBins<T> wb;
+  wb.nk = ba.nk;
+  wb.nwarps = (S::CT + 31) >> 5;
+  wb.b = reinterpret_cast<double*>(sm + N * TW);
+  wb.w = reinterpret_cast<T*>(wb.b + ba.nk);
+  wb.init();
+  const int c = threadIdx.x % TW, t = threadIdx.x / TW;
+  constexpr int ntz = NH / TW, ntiles = N * ntz;
+  constexpr int64_t si = (int64_t)N * NH;
+  __syncthreads();
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int j = tile / ntz, kz0 = (tile - j * ntz) * TW;
+    const int kz = kz0 + c;
+    const int64_t off = (int64_t)j * NH + kz;
+    C v[E];
+#pragma unroll
+    for (int e = 0; e < E; e++) v[e] = B[off + (t + Tc * e) * si];
+    fft_ct<C, E, N, kInterleaved, TW, -1>(v, sm, t, c, twf);
+    const int ny = sfreq<N>(j);
+    const C phy = ldg_c(phase + j), phz = ldg_c(phase + N + kz);
+    const T wyz = invw[j] * invw[N + kz];
+    const T mult = kz ? T(2) : T(1);
+#pragma unroll
+    for (int e = 0; e < E; e++) {
+      const int ii = t + Tc * e;
+      const int64_t addr = off + ii * si;
+      C X = v[e];
+      if (interlaced) {
+        const C A = F0[addr];
+        const C ph = cmul(cmul(ldg_c(phase + ii), phy), phz);
+        X = cscale(cadd(A, cmul(ph, X)), T(0.5));
+      }
+      if (compensate) X = cscale(X, invw[ii] * wyz);
+      const bool nyq = (ii == N / 2) || (j == N / 2);
+      if (roundtrip && nyq) X = mk(T(0), T(0));
+      F0[addr] = X;
+      if (!nyq) {
+        const int nx = sfreq<N>(ii);
+        const int n2 = nx * nx + ny * ny + kz * kz;
+        const int b = ba.bin_of_n2[n2];
+        if (b >= 0 && n2 > 0) wb.add(b, mult * (X.x * X.x + X.y * X.y));
+      }
+    }
+    __syncthreads();
+    wb.fold();
+    __syncthreads();
+  }
+  for (int b = threadIdx.x; b < ba.nk; b += blockDim.x) atomicAdd(&ba.bins[SLOT_P0 * ba.nk + b], wb.b[b]);
+}
+
+// ------------------------------------------------------------------ pass x + accumulate-and-bin
+// Per tile: F0 once (kept in shared memory, each thread its own modes); for each harmonic h
+// of the group, the x-pass of G_h and acc += Y_{l,m(h)}(khat) Re[G_h conj(F0)] per mode;
+// then mult * acc into the bins of `slot`.
+template <typename T, int N>
+__global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T>(Shape<N>::CT))
+    k_bin_x(const cx<T>* G, int64_t spec_stride, int ell, int h0, int M, const cx<T>* __restrict__ F0,
+            const cx<T>* __restrict__ twf, int slot, BinArgs ba, const __grid_constant__ YTab<T> yt) {
+  using C = cx<T>;
+  using S = Shape<N>;
+  constexpr int NH = S::NH, E = S::E, Tc = S::Tc, TW = S::TW;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  C* sF0 = sm + N * TW;
+  WarpBins<T> wb;
+  wb.nk = ba.nk;
+  wb.nwarps = (S::CT + 31) >> 5;
+  wb.b = reinterpret_cast<double*>(sF0 + N * TW);
+  wb.w = reinterpret_cast<T*>(wb.b + ba.nk);
+  wb.init();
+  const T sq2 = T(1.41421356237309504880);
+  const int c = threadIdx.x % TW, t = threadIdx.x / TW;
+  constexpr int ntz = NH / TW, ntiles = N * ntz;
+  constexpr int64_t si = (int64_t)N * NH;
+  __syncthreads();
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int j = tile / ntz, kz0 = (tile - j * ntz) * TW;
+    const int kz = kz0 + c;
+    const int64_t off = (int64_t)j * NH + kz;
+    const T fy = T(sfreq<N>(j)), fz = T(kz);
+    const T r2yz = fy * fy + fz * fz;
+    T acc[E];
+#pragma unroll
+    for (int e = 0; e < E; e++) {
+      sF0[(t + Tc * e) * TW + c] = F0[off + (t + Tc * e) * si];
+      acc[e] = T(0);
+    }
+    for (int s = 0; s < M; s++) {
+      const int h = h0 + s;
+      const int a = harm_a(h), sg = harm_sign(h);
+      const C* Gs = G + (int64_t)s * spec_stride;
+      C v[E];
+#pragma unroll
+      for (int e = 0; e < E; e++) v[e] = Gs[off + (t + Tc * e) * si];
+      fft_ct<C, E, N, kInterleaved, TW, -1>(v, sm, t, c, twf);
+#pragma unroll
+      for (int e = 0; e < E; e++) {
+        const T fx = T(sfreq<N>(t + Tc * e));
+        const T r2 = fx * fx + r2yz;
+        if (r2 == T(0)) continue;
+        const T inv = rsqrt_t<T>(r2);
+        const T x = fx * inv, y = fy * inv;
+        T Y = ylm_q<T>(yt, ell, a, fz * inv);
+        if (a > 0) {
+          T pr = x, pi = y;
+          for (int u = 1; u < a; u++) {
+            const T nr = pr * x - pi * y;
+            pi = pr * y + pi * x;
+            pr = nr;
+          }
+          Y = sq2 * Y * (sg > 0 ? pr : pi);
+        }
+        const C fv = sF0[(t + Tc * e) * TW + c];
+        acc[e] += Y * (v[e].x * fv.x + v[e].y * fv.y);
+      }
+    }
+    if (j != N / 2) {
+      const T mult = kz ? T(2) : T(1);
+      const int ny = sfreq<N>(j);
+#pragma unroll
+      for (int e = 0; e < E; e++) {
+        const int ii = t + Tc * e;
+        if (ii == N / 2) continue;
+        const int nx = sfreq<N>(ii);
+        const int n2 = nx * nx + ny * ny + kz * kz;
+        const int b = ba.bin_of_n2[n2];
+        if (b >= 0 && n2 > 0) wb.add(b, mult * acc[e]);
+      }
+    }
+    __syncthreads();
+    wb.fold();
+    __syncthreads();
+  }
+  for (int b = threadIdx.x; b < ba.nk; b += blockDim.x) atomicAdd(&ba.bins[slot * ba.nk + b], wb.b[b]);
+}
+
+// ------------------------------------------------------------------ launchers of one size
+template <typename K> static void set_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename T, int N> struct Passes {
+  using C = cx<T>;
+  using S = Shape<N>;
+  static size_t smem_col() { return (size_t)N * S::TW * sizeof(C); }
+  static size_t smem_bins(int nk) { return (size_t)nk * sizeof(double) + (size_t)((S::CT + 31) / 32) * nk * sizeof(T); }
+  static size_t smem_combine(int nk) { return smem_col() + smem_bins(nk); }
+  static size_t smem_bin(int nk) { return 2 * smem_col() + smem_bins(nk); }
+
+  static void r2c_z(const T* in, C* out, const C* twh, const C* twr, cudaStream_t s) {
+    const size_t smem = (size_t)S::ROWS * padded_len(S::NH) * sizeof(C);
+    set_smem(k_r2c_z<T, N>, smem);
+    k_r2c_z<T, N><<<N * N / S::ROWS, S::ZT, smem, s>>>(in, out, twh, twr);
+  }
+  static void c2r_z(const C* in, T* out, const C* twh, const C* twr, T scale, cudaStream_t s) {
+    const size_t smem = (size_t)S::ROWS * padded_len(S::NH) * sizeof(C);
+    set_smem(k_c2r_z<T, N>, smem);
+    k_c2r_z<T, N><<<N * N / S::ROWS, S::ZT, smem, s>>>(in, out, twh, twr, scale);
+  }
+  static size_t smem_ylm(int M, int rows) {
+    const size_t stage = (size_t)M * rows * N * sizeof(T);
+    const size_t xb = (size_t)M * rows * padded_len(S::NH) * sizeof(C);
+    return stage > xb ? stage : xb;
+  }
+  static void ylm_z(const T* f, C* out, int64_t stride, int ell, int h0, int M, const C* twh, const C* twr,
+                    const T* axis, int rows, cudaStream_t s) {
+    const size_t smem = smem_ylm(M, rows);
+    set_smem(k_ylm_r2c_z<T, N>, smem);
+    k_ylm_r2c_z<T, N><<<N * N / rows, M * rows * S::Tz, smem, s>>>(f, out, stride, ell, h0, M, twh, twr, axis, rows,
+                                                                    host_ytab<T>());
+  }
+  static void fft_y(C* data, int64_t stride, int nspec, const C* twf, int dir, cudaStream_t s) {
+    const size_t smem = smem_col();
+    dim3 grid(N * (S::NH / S::TW), nspec);
+    if (dir < 0) {
+      set_smem(k_fft_y<T, N, -1>, smem);
+      k_fft_y<T, N, -1><<<grid, S::CT, smem, s>>>(data, stride, twf);
+    } else {
+      set_smem(k_fft_y<T, N, 1>, smem);
+      k_fft_y<T, N, 1><<<grid, S::CT, smem, s>>>(data, stride, twf);
+    }
+  }
+  static void fft_x(const C* in, C* out, const C* twf, int dir, cudaStream_t s) {
+    const size_t smem = smem_col();
+    const unsigned grid = N * (S::NH / S::TW);
+    if (dir < 0) {
+      set_smem(k_fft_x<T, N, -1>, smem);
+      k_fft_x<T, N, -1><<<grid, S::CT, smem, s>>>(in, out, twf);
+    } else {
+      set_smem(k_fft_x<T, N, 1>, smem);
+      k_fft_x<T, N, 1><<<grid, S::CT, smem, s>>>(in, out, twf);
+    }
+  }
+  static void combine_x(const C* B, C* F0, const C* twf, int interlaced, int compensate, int roundtrip,
+                        const C* phase, const T* invw, const BinArgs& ba, int ctas, cudaStream_t s) {
+    const size_t smem = smem_combine(ba.nk);
+    set_smem(k_combine_x<T, N>, smem);
+    k_combine_x<T, N><<<ctas, S::CT, smem, s>>>(B, F0, twf, interlaced, compensate, roundtrip, phase, invw, ba);
+  }
+  static void bin_x(const C* G, int64_t stride, int ell, int h0, int M, const C* F0, const C* twf, int slot,
+                    const BinArgs& ba, int ctas, cudaStream_t s) {
+    const size_t smem = smem_bin(ba.nk);
+    set_smem(k_bin_x<T, N>, smem);
+    k_bin_x<T, N><<<ctas, S::CT, smem, s>>>(G, stride, ell, h0, M, F0, twf, slot, ba, host_ytab<T>());
+  }
+  static int ctas(int which, int nk, int nsm) {
+    int per = 0;
+    if (which == 0) {
+      const size_t smem = smem_combine(nk);
+      set_smem(k_combine_x<T, N>, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_combine_x<T, N>, S::CT, smem);
+    } else {
+      const size_t smem = smem_bin(nk);
+      set_smem(k_bin_x<T, N>, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bin_x<T, N>, S::CT, smem);
+    }
+    if (per < 1) per = 1;
+    const int ntiles = N * (S::NH / S::TW);
+    return per * nsm < ntiles ? per * nsm : ntiles;
+  }
+  static PassTable<T> table() {
+    PassTable<T> t;
+    t.N = N;
+    t.E = S::E;
+    t.tw = S::TW;
+    t.rows_z = S::ROWS;
+    t.tz = S::Tz;
+    t.r2c_z = &r2c_z;
+    t.c2r_z = &c2r_z;
+    t.ylm_z = &ylm_z;
+    t.smem_ylm = &smem_ylm;
+    t.fft_y = &fft_y;
+    t.fft_x = &fft_x;
+    t.combine_x = &combine_x;
+    t.bin_x = &bin_x;
+    t.ctas = &ctas;
+    t.smem_combine = &smem_combine;
+    t.smem_bin = &smem_bin;
+    return t;
+  }
+};
+
+#define PSPEC_DEFINE_PASSES(N_)                                                     \
+  template <> const PassTable<float>* pass_table_n<float, N_>() {                   \
+    static const PassTable<float> t = Passes<float, N_>::table();                   \
+    return &t;                                                                      \
+  }                                                                                 \
+  template <> const PassTable<double>* pass_table_n<double, N_>() {                 \
+    static const PassTable<double> t = Passes<double, N_>::table();                 \
+    return &t;                                                                      \
+  }
+
+}  // namespace pspec

@@ -50,32 +50,48 @@ template <typename T>
 void launch_paint(const PaintArgs& a, int window, int interlaced, int is_randoms, double* derived, T* mesh1,
                   T* mesh2, int N, int nblocks, cudaStream_t s);
 
-// Transform passes (E = register elements per thread: 8, or 24 for N = 3*2^a).
+// Transform passes, one table of launchers per supported mesh side N (pass_*.cu).
 // Tables: tw_half (L = N/2), tw_full (L = N), twr (exp(-2 pi i k/N), k < N/2).
-template <typename T>
-void launch_r2c_z(const T* in, cx<T>* out, const Geo& g, const FftPlan& pz, int E, const cx<T>* tw_half,
-                  const cx<T>* twr, int rows, cudaStream_t s);
-template <typename T>
-void launch_c2r_z(const cx<T>* in, T* out, const Geo& g, const FftPlan& pz, int E, const cx<T>* tw_half,
-                  const cx<T>* twr, int rows, T scale, cudaStream_t s);
-template <typename T>
-void launch_ylm_r2c_z(const T* f, cx<T>* out, int64_t spec_stride, int ell, int h0, int M, const Geo& g,
-                      const FftPlan& pz, int E, const cx<T>* tw_half, const cx<T>* twr, const T* axis_pos, int rows,
-                      int threads, cudaStream_t s);
-template <typename T>
-void launch_fft_y(cx<T>* data, int64_t spec_stride, int nspec, const Geo& g, const FftPlan& pf, int E,
-                  const cx<T>* tw_full, int tw, int dir, cudaStream_t s);
-template <typename T>
-void launch_fft_x(const cx<T>* in, cx<T>* out, const Geo& g, const FftPlan& pf, int E, const cx<T>* tw_full, int tw,
-                  int dir, cudaStream_t s);
-template <typename T>
-void launch_combine_x(const cx<T>* B, cx<T>* F0, const Geo& g, const FftPlan& pf, int E, const cx<T>* tw_full, int tw,
-                      int interlaced, int compensate, int roundtrip, const cx<T>* phase_axis, const T* invw_axis,
-                      const BinArgs& ba, int ctas, cudaStream_t s);
-template <typename T>
-void launch_bin_x(const cx<T>* G, int64_t spec_stride, int ell, int h0, int M, const cx<T>* F0, const Geo& g,
-                  const FftPlan& pf, int E, const cx<T>* tw_full, int tw, int slot, const BinArgs& ba, int ctas,
-                  cudaStream_t s);
+// Shapes fixed per N at compile time:
+//   col_tile(N): kz columns per y/x tile, a power of two dividing N/2 with at most 512
+//                threads (N/E per column) and at most 16 columns;
+//   z_rows(N):   rows per block of the plain z passes, a power of two dividing N^2 with at
+//                most 512 threads (N/(2E) per row).
+constexpr int elems_per_thread(int N) { return N % 3 == 0 ? 24 : 8; }
+constexpr int col_tile(int N) {
+  const int tc = N / elems_per_thread(N);
+  int cap = 512 / tc < 16 ? 512 / tc : 16, tw = 1;
+  while (tw * 2 <= cap && (N / 2) % (tw * 2) == 0) tw *= 2;
+  return tw;
+}
+constexpr int z_rows(int N) {
+  const int tz = (N / 2) / elems_per_thread(N);
+  int cap = 512 / tz, r = 1;
+  while (r * 2 <= cap && ((long long)N * N) % (r * 2) == 0) r *= 2;
+  return r;
+}
+
+template <typename T> struct PassTable {
+  int N, E, tw, rows_z, tz;
+  void (*r2c_z)(const T*, cx<T>*, const cx<T>*, const cx<T>*, cudaStream_t);
+  void (*c2r_z)(const cx<T>*, T*, const cx<T>*, const cx<T>*, T, cudaStream_t);
+  void (*ylm_z)(const T*, cx<T>*, int64_t, int, int, int, const cx<T>*, const cx<T>*, const T*, int, cudaStream_t);
+  size_t (*smem_ylm)(int, int);
+  void (*fft_y)(cx<T>*, int64_t, int, const cx<T>*, int, cudaStream_t);
+  void (*fft_x)(const cx<T>*, cx<T>*, const cx<T>*, int, cudaStream_t);
+  void (*combine_x)(const cx<T>*, cx<T>*, const cx<T>*, int, int, int, const cx<T>*, const T*, const BinArgs&, int,
+                    cudaStream_t);
+  void (*bin_x)(const cx<T>*, int64_t, int, int, int, const cx<T>*, const cx<T>*, int, const BinArgs&, int,
+                cudaStream_t);
+  int (*ctas)(int, int, int);  // (which: 0 combine, 1 bin; nk; SM count) -> persistent blocks
+  size_t (*smem_combine)(int);
+  size_t (*smem_bin)(int);
+};
+template <typename T, int N> const PassTable<T>* pass_table_n();
+// nullptr when N is not a supported mesh side.
+template <typename T> const PassTable<T>* pass_table(int N);
+// Y_lm recurrence coefficients (built in FP64 on the host), passed to kernels by value.
+template <typename T> const YTab<T>& host_ytab();
 
 // Mode counts: cnt[|n|^2] over binnable modes (once per plan), then N_b and sum |k| per bin.
 void launch_mode_counts(const Geo& g, unsigned int* cnt, int nsm, cudaStream_t s);
@@ -92,16 +108,5 @@ struct WedgeTab {
   double lbar[kMaxWedgeTab];  // [i * n_mu + w]
 };
 void launch_wedges(const double* P, int n_ells, int nk, int n_mu, const WedgeTab& t, double* out, cudaStream_t s);
-
-// Shared-memory sizes and persistent CTA counts (which: 0 combine, 1 bin).
-size_t smem_rows(int L, int rows, size_t csz);
-template <typename T> size_t smem_cols(const Geo& g, int tw);
-template <typename T> size_t smem_ylm_z(const Geo& g, int E, int M, int rows, int threads);
-template <typename T> size_t smem_combine(const Geo& g, int E, int tw, int nk);
-template <typename T> size_t smem_bin_x(const Geo& g, int E, int tw, int nk);
-template <typename T> int persistent_ctas(int which, const Geo& g, int E, int tw, int nk, int nsm);
-
-// Y_lm coefficient tables (FP64-built) into constant memory of the current device.
-cudaError_t upload_ylm_tables(cudaStream_t s);
 
 }  // namespace pspec

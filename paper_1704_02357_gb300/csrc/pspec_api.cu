@@ -15,7 +15,6 @@ namespace {
 
 constexpr size_t kAlign = 256;
 constexpr size_t kSmemBudget = 200 * 1024;   // one block
-constexpr size_t kSmemShared = 100 * 1024;   // two blocks per SM
 constexpr int kMaxElls = PSPEC_MAX_ELL / 2 + 1;
 constexpr int kYlmMaxThreads = 512;
 
@@ -31,35 +30,6 @@ bool good_nmesh(int n) {
   return x == 3 && n >= 48;
 }
 
-int elems_per_thread(int N) { return N % 3 == 0 ? 24 : 8; }
-
-// Radices dividing E, largest first; the factor 3 (if any) last.
-FftPlan make_fft(int L) {
-  FftPlan p{};
-  p.L = L;
-  int x = L, ns = 1;
-  auto push = [&](int r) {
-    p.rad[p.nst] = r;
-    p.ns[p.nst] = ns;
-    ns *= r;
-    p.nst++;
-    x /= r;
-  };
-  int three = 0;
-  while (x % 3 == 0) {
-    x /= 3;
-    three++;
-  }
-  while (x % 8 == 0) push(8);
-  while (x % 4 == 0) push(4);
-  while (x % 2 == 0) push(2);
-  for (int i = 0; i < three; i++) {
-    x *= 3;
-    push(3);
-  }
-  return p;
-}
-
 int pow2_floor(int v) {
   int p = 1;
   while (p * 2 <= v) p *= 2;
@@ -71,7 +41,8 @@ struct Plan {
   int E;
   int esz;  // sizeof(T)
   size_t csz;
-  FftPlan pz, pf;
+  const PassTable<float>* tf;
+  const PassTable<double>* td;
   int tw_y, tw_comb, tw_bin, rows_z;
   int group_max, ylm_rows_max;
   int ctas_comb, ctas_bin;
@@ -83,19 +54,6 @@ struct Plan {
   size_t o_mesh1, o_mesh2, o_f0, o_w, o_f, o_g, o_twh, o_twf, o_twr, o_axis, o_phase, o_invw, o_bin, o_kmag, o_cnt,
       o_lo, o_hi, o_nmodes, o_ksum, o_sums, o_derived, o_bins, o_out, total;
 };
-
-// Column tiles: TW kz columns x N/E threads each, at most 1024 threads (512 preferred) and
-// the shared-memory budget.
-int pick_tw(const Plan& pl, int per_col_bytes, size_t fixed, size_t budget, int max_threads) {
-  const int N = pl.g.N, NH = pl.g.NH, Tc = N / pl.E;
-  for (int tw = 16; tw >= 1; tw >>= 1) {
-    if (NH % tw) continue;
-    if (tw * Tc > max_threads) continue;
-    if (fixed + (size_t)per_col_bytes * tw > budget) continue;
-    return tw;
-  }
-  return 1;
-}
 
 pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl, std::string* why) {
   if (!p) { *why = "params is NULL"; return PSPEC_EINVAL; }
@@ -119,21 +77,16 @@ pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl,
   pl->esz = f64 ? 8 : 4;
   pl->csz = f64 ? 16 : 8;
   const size_t csz = pl->csz;
-  pl->pz = make_fft(NH);
-  pl->pf = make_fft(N);
+  pl->tf = pass_table<float>(N);
+  pl->td = pass_table<double>(N);
+  if (!pl->tf || !pl->td) { *why = "no compiled transform passes for this nmesh"; return PSPEC_EUNSUPPORTED; }
   pl->roundtrip = p->interlaced || p->compensate;
   pl->Sr = (size_t)N * N * N * pl->esz;
   pl->Sc = (size_t)N * N * NH * csz;
   pl->n2max = 3 * NH * NH;
 
-  const size_t bins_bytes = (size_t)max_kbins * (8 + pl->esz * 32);  // FP64 bins + up to 32 warps of partials
-  pl->tw_y = pick_tw(*pl, N * (int)csz, 0, kSmemShared, 512);
-  pl->tw_comb = pick_tw(*pl, N * (int)csz, bins_bytes, kSmemBudget, 512);
-  pl->tw_bin = pick_tw(*pl, 2 * N * (int)csz, bins_bytes, kSmemBudget, 512);
-  const int Tz = NH / pl->E;
-  pl->rows_z = std::max(1, pow2_floor(std::max(1, 512 / Tz)));
-  while (pl->rows_z > 1 && (((int64_t)N * N) % pl->rows_z || smem_rows(NH, pl->rows_z, csz) > kSmemShared))
-    pl->rows_z >>= 1;
+  pl->tw_y = pl->tw_comb = pl->tw_bin = pl->tf->tw;
+  pl->rows_z = pl->tf->rows_z;
 
   // harmonics per group (spectra buffered between the z and x passes): bounded by memory
   const int nharm = 2 * p->ell_max + 1;
@@ -141,11 +94,11 @@ pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl,
   pl->group_max = p->ell_max == 0 ? 0 : std::max(1, std::min(nharm, m_mem));
 
   if (f64) {
-    pl->ctas_comb = persistent_ctas<double>(0, pl->g, pl->E, pl->tw_comb, max_kbins, nsm);
-    pl->ctas_bin = persistent_ctas<double>(1, pl->g, pl->E, pl->tw_bin, max_kbins, nsm);
+    pl->ctas_comb = pl->td->ctas(0, max_kbins, nsm);
+    pl->ctas_bin = pl->td->ctas(1, max_kbins, nsm);
   } else {
-    pl->ctas_comb = persistent_ctas<float>(0, pl->g, pl->E, pl->tw_comb, max_kbins, nsm);
-    pl->ctas_bin = persistent_ctas<float>(1, pl->g, pl->E, pl->tw_bin, max_kbins, nsm);
+    pl->ctas_comb = pl->tf->ctas(0, max_kbins, nsm);
+    pl->ctas_bin = pl->tf->ctas(1, max_kbins, nsm);
   }
   pl->nblk_sum = 2 * nsm;
 
@@ -430,7 +383,8 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
   using C = cx<T>;
   const Plan& pl = c->pl;
   const Geo& g = pl.g;
-  const int N = g.N, E = pl.E;
+  const int N = g.N;
+  const PassTable<T>* PT = pass_table<T>(N);
   cudaStream_t s = c->stream;
   T* m1 = c->at<T>(pl.o_mesh1);
   T* m2 = c->at<T>(pl.o_mesh2);
@@ -459,29 +413,27 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
   };
 
   // a3: F1 (and F2), combine + compensate -> F0 with the l = 0 sums; round trip -> f
-  TRY(run(c, PSPEC_K_FFT_Z, acc(Sr + Sc), [&] { launch_r2c_z<T>(m1, F0, g, pl.pz, E, twh, twr, pl.rows_z, s); }));
-  TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { launch_fft_y<T>(F0, 0, 1, g, pl.pf, E, twf, pl.tw_y, -1, s); }));
+  TRY(run(c, PSPEC_K_FFT_Z, acc(Sr + Sc), [&] { PT->r2c_z(m1, F0, twh, twr, s); }));
+  TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { PT->fft_y(F0, 0, 1, twf, -1, s); }));
   transforms++;
   if (c->p.interlaced) {
-    TRY(run(c, PSPEC_K_FFT_X, acc(2 * Sc), [&] { launch_fft_x<T>(F0, F0, g, pl.pf, E, twf, pl.tw_y, -1, s); }));
-    TRY(run(c, PSPEC_K_FFT_Z, acc(Sr + Sc), [&] { launch_r2c_z<T>(m2, W, g, pl.pz, E, twh, twr, pl.rows_z, s); }));
-    TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { launch_fft_y<T>(W, 0, 1, g, pl.pf, E, twf, pl.tw_y, -1, s); }));
+    TRY(run(c, PSPEC_K_FFT_X, acc(2 * Sc), [&] { PT->fft_x(F0, F0, twf, -1, s); }));
+    TRY(run(c, PSPEC_K_FFT_Z, acc(Sr + Sc), [&] { PT->r2c_z(m2, W, twh, twr, s); }));
+    TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { PT->fft_y(W, 0, 1, twf, -1, s); }));
     transforms++;
     TRY(run(c, PSPEC_K_COMBINE, acc(3 * Sc), [&] {
-      launch_combine_x<T>(W, F0, g, pl.pf, E, twf, pl.tw_comb, 1, c->p.compensate, pl.roundtrip, phase, invw, ba,
-                          pl.ctas_comb, s);
+      PT->combine_x(W, F0, twf, 1, c->p.compensate, pl.roundtrip, phase, invw, ba, pl.ctas_comb, s);
     }));
   } else {
     TRY(run(c, PSPEC_K_COMBINE, acc(2 * Sc), [&] {
-      launch_combine_x<T>(F0, F0, g, pl.pf, E, twf, pl.tw_comb, 0, c->p.compensate, pl.roundtrip, phase, invw, ba,
-                          pl.ctas_comb, s);
+      PT->combine_x(F0, F0, twf, 0, c->p.compensate, pl.roundtrip, phase, invw, ba, pl.ctas_comb, s);
     }));
   }
   if (pl.roundtrip) {
-    TRY(run(c, PSPEC_K_FFT_X, acc(2 * Sc), [&] { launch_fft_x<T>(F0, W, g, pl.pf, E, twf, pl.tw_y, +1, s); }));
-    TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { launch_fft_y<T>(W, 0, 1, g, pl.pf, E, twf, pl.tw_y, +1, s); }));
+    TRY(run(c, PSPEC_K_FFT_X, acc(2 * Sc), [&] { PT->fft_x(F0, W, twf, +1, s); }));
+    TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { PT->fft_y(W, 0, 1, twf, +1, s); }));
     const T scale = T(2.0 / ((double)N * N * N));
-    TRY(run(c, PSPEC_K_C2R_Z, acc(Sc + Sr), [&] { launch_c2r_z<T>(W, f, g, pl.pz, E, twh, twr, pl.rows_z, scale, s); }));
+    TRY(run(c, PSPEC_K_C2R_Z, acc(Sc + Sr), [&] { PT->c2r_z(W, f, twh, twr, scale, s); }));
     transforms++;
   }
 
@@ -495,23 +447,20 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
     const int nh = 2 * ell + 1;
     for (int h0 = 0; h0 < nh; h0 += pl.group_max) {
       const int M = std::min(pl.group_max, nh - h0);
-      // z pass with the Y_lm weights: one block holds Ms harmonics x rows rows, Tz threads each
-      const int Tz = g.NH / E;
-      const int ms_max = std::max(1, kYlmMaxThreads / Tz);
+      // z pass with the Y_lm weights: one block holds Ms harmonics x rows rows, tz threads each
+      const int tz = PT->tz;
+      const int ms_max = std::max(1, kYlmMaxThreads / tz);
       for (int hs = 0; hs < M; hs += ms_max) {
         const int Ms = std::min(ms_max, M - hs);
-        int rows = std::max(1, pow2_floor(std::max(1, kYlmMaxThreads / (Ms * Tz))));
-        while (rows > 1 && (((int64_t)N * N) % rows ||
-                            (pl.esz == 4 ? smem_ylm_z<float>(g, E, Ms, rows, 0)
-                                         : smem_ylm_z<double>(g, E, Ms, rows, 0)) > kSmemBudget))
-          rows >>= 1;
+        int rows = std::max(1, pow2_floor(std::max(1, kYlmMaxThreads / (Ms * tz))));
+        while (rows > 1 && (((int64_t)N * N) % rows || PT->smem_ylm(Ms, rows) > kSmemBudget)) rows >>= 1;
         TRY(run(c, PSPEC_K_YLM_Z, acc(Sr + Ms * Sc), [&] {
-          launch_ylm_r2c_z<T>(f, G + hs * stride, stride, ell, h0 + hs, Ms, g, pl.pz, E, twh, twr, axis, rows, 0, s);
+          PT->ylm_z(f, G + hs * stride, stride, ell, h0 + hs, Ms, twh, twr, axis, rows, s);
         }));
       }
-      TRY(run(c, PSPEC_K_FFT_Y, acc(2 * M * Sc), [&] { launch_fft_y<T>(G, stride, M, g, pl.pf, E, twf, pl.tw_y, -1, s); }));
+      TRY(run(c, PSPEC_K_FFT_Y, acc(2 * M * Sc), [&] { PT->fft_y(G, stride, M, twf, -1, s); }));
       TRY(run(c, PSPEC_K_BIN_X, acc(Sc + M * Sc), [&] {
-        launch_bin_x<T>(G, stride, ell, h0, M, F0, g, pl.pf, E, twf, pl.tw_bin, SLOT_ELL0 + i, ba, pl.ctas_bin, s);
+        PT->bin_x(G, stride, ell, h0, M, F0, twf, SLOT_ELL0 + i, ba, pl.ctas_bin, s);
       }));
       transforms += M;
     }
@@ -598,11 +547,6 @@ pspec_status pspec_create(const pspec_params* p, int32_t device, void* stream, v
   c->ws_bytes = workspace_bytes;
   c->max_kbins = max_kbins;
   c->nsm = nsm;
-  cudaError_t e = upload_ylm_tables(c->stream);
-  if (e != cudaSuccess) {
-    delete c;
-    return PSPEC_ECUDA;
-  }
   st = c->p.precision == PSPEC_FP64 ? upload_tables<double>(c) : upload_tables<float>(c);
   if (st != PSPEC_OK) {
     delete c;
