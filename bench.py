@@ -307,7 +307,7 @@ def main():
     def est_for(precision, ell_max):
         return Estimator(nmesh=nmesh, box_size=BOX, box_corner=corner, observer=(0.0, 0.0, 0.0), window="cic",
                          interlaced=True, compensate=True, precision=precision, ell_max=ell_max, P0=P0, nbar=NBAR,
-                         max_kbins=nk, device=dev, stream=stream)
+                         max_kbins=nk, max_particles=int(data.size + randoms.size), device=dev, stream=stream)
 
     dpos = torch.as_tensor(data.pos, device=dev)
     rpos = torch.as_tensor(randoms.pos, device=dev)

@@ -80,6 +80,8 @@ typedef struct {
   double P0;               /* FKP P0; 0 gives w_fkp = 1 */
   double nbar;             /* n̄ used for particles whose catalog has no nbar array */
   int64_t max_group_bytes; /* cap on the per-group spectrum buffers; 0 = one whole multipole */
+  int64_t max_particles;   /* data + randoms the tile-binned paint is sized for (FP32 meshes);
+                              0, a larger catalog pair or FP64 meshes use direct atomic painting */
 } pspec_params;
 
 typedef struct {

@@ -307,6 +307,236 @@ template void launch_paint<float>(const PaintArgs&, int, int, int, double*, floa
 template void launch_paint<double>(const PaintArgs&, int, int, int, double*, double*, double*, int, int,
                                    cudaStream_t);
 
+// ------------------------------------------------------------------ a2: tile-binned painting
+// FP32 meshes. Particles of both catalogs are counting-sorted by the 16^3-cell tile that
+// holds their (mesh 1) base node; one block per non-empty tile then accumulates the tile and
+// a 2-cell halo in shared memory (both interlaced meshes) and adds it into the global meshes
+// once. Per particle the 24-bit fixed-point grid coordinate is kept as a record
+// {(cell in tile << 24) | fraction, x3; value}.
+constexpr int kPT = 16;             // tile side (cells)
+constexpr int kPH = 2;              // halo on each side
+constexpr int kPS = kPT + 2 * kPH;  // shared tile side
+constexpr int kPS3 = kPS * kPS * kPS;
+constexpr unsigned kNoTile = 0xffffffffu;
+
+template <int WIN>
+__global__ void __launch_bounds__(256) k_ptile_prep(PaintArgs a, int is_randoms, double* __restrict__ derived,
+                                                    TileArgs ta, int64_t offset, int N) {
+  const double sign = is_randoms ? -derived[D_ALPHA] : 1.0;
+  const bool uniform = (a.weight == nullptr) && (a.nbar == nullptr);
+  const float v_uniform = (float)(sign * a.wf_default);
+  const double lim = (double)N;
+  const int nts = N / kPT;
+  unsigned bad = 0, out = 0;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.count;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    double x, y, z;
+    load_pos(a, p, x, y, z);
+    double wc = 1.0, nb = a.nbar_default;
+    if (!uniform) {
+      wc = a.weight ? a.weight[p] : 1.0;
+      nb = a.nbar ? a.nbar[p] : a.nbar_default;
+    }
+    const double u[3] = {(x - a.corner[0]) * a.inv_cell, (y - a.corner[1]) * a.inv_cell,
+                         (z - a.corner[2]) * a.inv_cell};
+    if (!(fabs(u[0]) < kMaxCells && fabs(u[1]) < kMaxCells && fabs(u[2]) < kMaxCells && isfinite(wc) &&
+          isfinite(nb))) {
+      bad++;
+      ta.tile_of[offset + p] = kNoTile;
+      continue;
+    }
+    if (u[0] < 0.0 || u[0] >= lim || u[1] < 0.0 || u[1] >= lim || u[2] < 0.0 || u[2] >= lim) out++;
+    const float v = uniform ? v_uniform : (float)(sign * wc * fkp_w(a, nb));
+    unsigned packed[3];
+    int tc[3];
+    for (int d = 0; d < 3; d++) {
+      const int64_t U = __double2ll_rn(u[d] * 16777216.0);
+      // base node of mesh 1: floor(u) (CIC) or floor(u + 1/2) (TSC); fraction relative to
+      // that node (CIC) or to that node - 1/2 (TSC), in [0, 2^24)
+      const int64_t c = WIN == PSPEC_WINDOW_CIC ? (U >> 24) : ((U + (1ll << 23)) >> 24);
+      const unsigned f = (unsigned)(U - c * 16777216ll + (WIN == PSPEC_WINDOW_CIC ? 0 : (1ll << 23)));
+      const int cw = wrap(c, N);
+      tc[d] = cw / kPT;
+      packed[d] = ((unsigned)(cw - tc[d] * kPT) << 24) | f;
+    }
+    const unsigned tile = (unsigned)((tc[0] * nts + tc[1]) * nts + tc[2]);
+    ta.rec[offset + p] = make_uint4(packed[0], packed[1], packed[2], __float_as_uint(v));
+    ta.tile_of[offset + p] = tile;
+    atomicAdd(&ta.cnt[tile], 1u);
+  }
+  const unsigned nb_w = __reduce_add_sync(0xffffffffu, bad);
+  const unsigned no_w = __reduce_add_sync(0xffffffffu, out);
+  if ((threadIdx.x & 31) == 0) {
+    if (nb_w) atomicAdd(&derived[D_NONFINITE], (double)nb_w);
+    if (no_w) atomicAdd(&derived[D_WRAPPED], (double)no_w);
+  }
+}
+
+// Exclusive prefix sum of the tile counts (one block): off[] and cursor[].
+__global__ void __launch_bounds__(1024) k_ptile_scan(TileArgs ta, int ntiles) {
+  __shared__ unsigned part[1024];
+  const int per = (ntiles + blockDim.x - 1) / blockDim.x;
+  const int b0 = threadIdx.x * per;
+  unsigned s = 0;
+  for (int i = b0; i < b0 + per && i < ntiles; i++) s += ta.cnt[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+    const unsigned add = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += add;
+    __syncthreads();
+  }
+  unsigned run = part[threadIdx.x] - s;
+  for (int i = b0; i < b0 + per && i < ntiles; i++) {
+    ta.off[i] = run;
+    ta.cursor[i] = run;
+    run += ta.cnt[i];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_ptile_scatter(TileArgs ta, int64_t total) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned t = ta.tile_of[p];
+    if (t == kNoTile) continue;
+    const unsigned pos = atomicAdd(&ta.cursor[t], 1u);
+    ta.sorted[pos] = ta.rec[p];
+  }
+}
+
+// Tile-local node indices (0 .. kPS-1) and weights along one axis from the tile-local
+// fixed-point coordinate V (2^24 per cell; V = 0 at the tile's first cell).
+template <int WIN>
+__device__ __forceinline__ void tile_nodes(int V, int* idx, float* w) {
+  if (WIN == PSPEC_WINDOW_CIC) {
+    const int c = V >> 24;
+    const float d = (float)(V - c * 16777216) * 5.9604644775390625e-8f;
+    w[0] = 1.f - d;
+    w[1] = d;
+    idx[0] = c + kPH;
+    idx[1] = c + 1 + kPH;
+  } else {
+    const int c = (V + (1 << 23)) >> 24;
+    const float d = (float)(V - c * 16777216) * 5.9604644775390625e-8f;
+    w[0] = 0.5f * (0.5f - d) * (0.5f - d);
+    w[1] = 0.75f - d * d;
+    w[2] = 0.5f * (0.5f + d) * (0.5f + d);
+    idx[0] = c - 1 + kPH;
+    idx[1] = c + kPH;
+    idx[2] = c + 1 + kPH;
+  }
+}
+
+template <int WIN>
+__device__ __forceinline__ void tile_scatter(float* st, const int (&ix)[3], const int (&iy)[3], const int (&iz)[3],
+                                             const float (&wx)[3], const float (&wy)[3], const float (&wz)[3],
+                                             float v) {
+  constexpr int K = WIN == PSPEC_WINDOW_CIC ? 2 : 3;
+#pragma unroll
+  for (int a = 0; a < K; a++) {
+    const float va = v * wx[a];
+#pragma unroll
+    for (int b = 0; b < K; b++) {
+      const float vb = va * wy[b];
+      float* row = st + (ix[a] * kPS + iy[b]) * kPS;
+#pragma unroll
+      for (int c = 0; c < K; c++) atomicAdd(row + iz[c], vb * wz[c]);
+    }
+  }
+}
+
+template <int WIN, bool INTER>
+__global__ void __launch_bounds__(256) k_ptile_paint(TileArgs ta, float* __restrict__ m1, float* __restrict__ m2,
+                                                     int N) {
+  extern __shared__ float st[];  // [INTER ? 2 : 1][kPS^3]
+  const int tile = blockIdx.x;
+  const unsigned n = ta.cnt[tile];
+  if (n == 0) return;
+  const unsigned o = ta.off[tile];
+  constexpr int NM = INTER ? 2 : 1;
+  for (int i = threadIdx.x; i < NM * kPS3; i += blockDim.x) st[i] = 0.f;
+  __syncthreads();
+  for (unsigned q = threadIdx.x; q < n; q += blockDim.x) {
+    const uint4 r = ta.sorted[o + q];
+    const float v = __uint_as_float(r.w);
+    // tile-local fixed-point coordinate of the particle (mesh 1)
+    const int off1 = WIN == PSPEC_WINDOW_CIC ? 0 : (1 << 23);
+    const int V[3] = {(int)((r.x >> 24) << 24) + (int)(r.x & 0xffffffu) - off1,
+                      (int)((r.y >> 24) << 24) + (int)(r.y & 0xffffffu) - off1,
+                      (int)((r.z >> 24) << 24) + (int)(r.z & 0xffffffu) - off1};
+    int ix[3], iy[3], iz[3];
+    float wx[3], wy[3], wz[3];
+    tile_nodes<WIN>(V[0], ix, wx);
+    tile_nodes<WIN>(V[1], iy, wy);
+    tile_nodes<WIN>(V[2], iz, wz);
+    tile_scatter<WIN>(st, ix, iy, iz, wx, wy, wz, v);
+    if (INTER) {
+      const int h = 1 << 23;  // half a cell
+      tile_nodes<WIN>(V[0] - h, ix, wx);
+      tile_nodes<WIN>(V[1] - h, iy, wy);
+      tile_nodes<WIN>(V[2] - h, iz, wz);
+      tile_scatter<WIN>(st + kPS3, ix, iy, iz, wx, wy, wz, v);
+    }
+  }
+  __syncthreads();
+  const int nts = N / kPT;
+  const int tz = tile % nts, ty = (tile / nts) % nts, tx = tile / (nts * nts);
+  const int gx0 = tx * kPT - kPH, gy0 = ty * kPT - kPH, gz0 = tz * kPT - kPH;
+  for (int i = threadIdx.x; i < NM * kPS3; i += blockDim.x) {
+    const float val = st[i];
+    if (val == 0.f) continue;
+    const int mesh = i / kPS3, cell = i - mesh * kPS3;
+    const int lx = cell / (kPS * kPS), ly = (cell / kPS) % kPS, lz = cell % kPS;
+    const int gx = wrap(gx0 + lx, N), gy = wrap(gy0 + ly, N), gz = wrap(gz0 + lz, N);
+    float* m = mesh ? m2 : m1;
+    atomicAdd(m + ((int64_t)gx * N + gy) * N + gz, val);
+  }
+}
+
+void launch_ptile_prep(const PaintArgs& a, int window, int is_randoms, double* derived, const TileArgs& ta,
+                       int64_t offset, int N, int nblocks, cudaStream_t s) {
+  if (a.count <= 0) return;
+  const int64_t need = (a.count + 255) / 256;
+  const int nb = (int)(need < nblocks ? need : nblocks);
+  if (window == PSPEC_WINDOW_CIC)
+    k_ptile_prep<PSPEC_WINDOW_CIC><<<nb, 256, 0, s>>>(a, is_randoms, derived, ta, offset, N);
+  else
+    k_ptile_prep<PSPEC_WINDOW_TSC><<<nb, 256, 0, s>>>(a, is_randoms, derived, ta, offset, N);
+}
+
+void launch_ptile_scan(const TileArgs& ta, int ntiles, cudaStream_t s) { k_ptile_scan<<<1, 1024, 0, s>>>(ta, ntiles); }
+
+void launch_ptile_scatter(const TileArgs& ta, int64_t total, int nblocks, cudaStream_t s) {
+  if (total <= 0) return;
+  const int64_t need = (total + 255) / 256;
+  const int nb = (int)(need < nblocks ? need : nblocks);
+  k_ptile_scatter<<<nb, 256, 0, s>>>(ta, total);
+}
+
+template <typename K> static void set_smem_attr(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+void launch_ptile_paint(const TileArgs& ta, int window, int interlaced, float* m1, float* m2, int N, cudaStream_t s) {
+  const int ntiles = (N / kPT) * (N / kPT) * (N / kPT);
+  const size_t smem = (size_t)(interlaced ? 2 : 1) * kPS3 * sizeof(float);
+  if (window == PSPEC_WINDOW_CIC) {
+    if (interlaced) {
+      set_smem_attr(k_ptile_paint<PSPEC_WINDOW_CIC, true>, smem);
+      k_ptile_paint<PSPEC_WINDOW_CIC, true><<<ntiles, 256, smem, s>>>(ta, m1, m2, N);
+    } else {
+      k_ptile_paint<PSPEC_WINDOW_CIC, false><<<ntiles, 256, smem, s>>>(ta, m1, m2, N);
+    }
+  } else {
+    if (interlaced) {
+      set_smem_attr(k_ptile_paint<PSPEC_WINDOW_TSC, true>, smem);
+      k_ptile_paint<PSPEC_WINDOW_TSC, true><<<ntiles, 256, smem, s>>>(ta, m1, m2, N);
+    } else {
+      k_ptile_paint<PSPEC_WINDOW_TSC, false><<<ntiles, 256, smem, s>>>(ta, m1, m2, N);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ a6: finalise
 struct EllList {
   int n;

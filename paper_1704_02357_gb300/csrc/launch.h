@@ -50,6 +50,23 @@ template <typename T>
 void launch_paint(const PaintArgs& a, int window, int interlaced, int is_randoms, double* derived, T* mesh1,
                   T* mesh2, int N, int nblocks, cudaStream_t s);
 
+// a2, tile-binned (FP32 meshes): prep (records + tile counts) per catalog, scan, scatter
+// into tile order, then one block per non-empty 16^3 tile. Tile side kPaintTile divides N.
+constexpr int kPaintTile = 16;
+struct TileArgs {
+  unsigned* cnt;     // [ntiles] particles per tile (cleared before prep)
+  unsigned* off;     // [ntiles] exclusive prefix of cnt
+  unsigned* cursor;  // [ntiles] scatter cursors
+  uint4* rec;        // [particles] records in input order
+  unsigned* tile_of; // [particles] tile of each record (all ones: left out)
+  uint4* sorted;     // [particles] records in tile order
+};
+void launch_ptile_prep(const PaintArgs& a, int window, int is_randoms, double* derived, const TileArgs& ta,
+                       int64_t offset, int N, int nblocks, cudaStream_t s);
+void launch_ptile_scan(const TileArgs& ta, int ntiles, cudaStream_t s);
+void launch_ptile_scatter(const TileArgs& ta, int64_t total, int nblocks, cudaStream_t s);
+void launch_ptile_paint(const TileArgs& ta, int window, int interlaced, float* m1, float* m2, int N, cudaStream_t s);
+
 // Transform passes, one table of launchers per supported mesh side N (pass_*.cu).
 // Tables: tw_half (L = N/2), tw_full (L = N), twr (exp(-2 pi i k/N), k < N/2).
 // Shapes fixed per N at compile time:

@@ -52,7 +52,10 @@ struct Plan {
   int n2max;
   // workspace offsets
   size_t o_mesh1, o_mesh2, o_f0, o_w, o_f, o_g, o_twh, o_twf, o_twr, o_axis, o_phase, o_invw, o_bin, o_kmag, o_cnt,
-      o_lo, o_hi, o_nmodes, o_ksum, o_sums, o_derived, o_bins, o_out, total;
+      o_lo, o_hi, o_nmodes, o_ksum, o_sums, o_derived, o_bins, o_out, o_tcnt, o_toff, o_tcur, o_prec, o_ptile,
+      o_psort, total;
+  int64_t max_particles;  // capacity of the tile-binned paint (0: direct painting only)
+  int ntiles;
 };
 
 pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl, std::string* why) {
@@ -68,6 +71,7 @@ pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl,
   if (!(std::isfinite(p->P0) && p->P0 >= 0) || !(std::isfinite(p->nbar) && p->nbar >= 0)) { *why = "P0 and nbar must be finite and >= 0"; return PSPEC_EINVAL; }
   if (max_kbins < 1 || max_kbins > PSPEC_MAX_KBINS) { *why = "max_kbins out of range"; return PSPEC_EINVAL; }
   if (p->max_group_bytes < 0) { *why = "max_group_bytes < 0"; return PSPEC_EINVAL; }
+  if (p->max_particles < 0 || p->max_particles > (int64_t)0xfffffff0) { *why = "max_particles out of range"; return PSPEC_EINVAL; }
 
   const bool f64 = p->precision == PSPEC_FP64;
   const int N = p->nmesh, NH = N / 2;
@@ -131,6 +135,16 @@ pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl,
   pl->o_derived = take(D_COUNT * sizeof(double));
   pl->o_bins = take((size_t)(SLOT_ELL0 + kMaxElls) * max_kbins * sizeof(double));
   pl->o_out = take(((size_t)kMaxElls + 2) * max_kbins * sizeof(double));
+  pl->max_particles = f64 ? 0 : p->max_particles;
+  pl->ntiles = (N / kPaintTile) * (N / kPaintTile) * (N / kPaintTile);
+  if (pl->max_particles > 0) {
+    pl->o_tcnt = take((size_t)pl->ntiles * sizeof(unsigned));
+    pl->o_toff = take((size_t)pl->ntiles * sizeof(unsigned));
+    pl->o_tcur = take((size_t)pl->ntiles * sizeof(unsigned));
+    pl->o_prec = take((size_t)pl->max_particles * 16);
+    pl->o_ptile = take((size_t)pl->max_particles * sizeof(unsigned));
+    pl->o_psort = take((size_t)pl->max_particles * 16);
+  }
   pl->total = o;
   return PSPEC_OK;
 }
@@ -366,6 +380,33 @@ pspec_status do_paint(Ctx* c, const pspec_catalog* d, const pspec_catalog* r) {
   // algorithmic bytes of painting: the particles once and each mesh written once
   const int nb = 16 * c->nsm;
   const double nmesh = c->p.interlaced ? 2.0 : 1.0;
+  const int64_t total = d->count + r->count;
+  if (sizeof(T) == 4 && pl.max_particles > 0 && total <= pl.max_particles) {
+    TileArgs ta;
+    ta.cnt = c->at<unsigned>(pl.o_tcnt);
+    ta.off = c->at<unsigned>(pl.o_toff);
+    ta.cursor = c->at<unsigned>(pl.o_tcur);
+    ta.rec = c->at<uint4>(pl.o_prec);
+    ta.tile_of = c->at<unsigned>(pl.o_ptile);
+    ta.sorted = c->at<uint4>(pl.o_psort);
+    e = cudaMemsetAsync(ta.cnt, 0, (size_t)pl.ntiles * sizeof(unsigned), c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tile counts clear");
+    float* f1 = reinterpret_cast<float*>(m1);
+    float* f2 = reinterpret_cast<float*>(m2);
+    TRY(run(c, PSPEC_K_PAINT, cat_bytes(d), [&] {
+      launch_ptile_prep(ad, c->p.window, 0, der, ta, 0, N, nb, c->stream);
+    }));
+    TRY(run(c, PSPEC_K_PAINT, cat_bytes(r), [&] {
+      launch_ptile_prep(ar, c->p.window, 1, der, ta, d->count, N, nb, c->stream);
+    }));
+    TRY(run(c, PSPEC_K_PAINT, 0.0, [&] { launch_ptile_scan(ta, pl.ntiles, c->stream); }));
+    TRY(run(c, PSPEC_K_PAINT, 0.0, [&] { launch_ptile_scatter(ta, total, nb, c->stream); }));
+    TRY(run(c, PSPEC_K_PAINT, nmesh * pl.Sr, [&] {
+      launch_ptile_paint(ta, c->p.window, c->p.interlaced, f1, f2, N, c->stream);
+    }));
+    c->bytes_paint = bytes + cat_bytes(d) + cat_bytes(r) + nmesh * pl.Sr;
+    return PSPEC_OK;
+  }
   const double frac_d = (double)d->count / (double)(d->count + r->count);
   if (d->count > 0)
     TRY(run(c, PSPEC_K_PAINT, cat_bytes(d) + frac_d * nmesh * pl.Sr, [&] {

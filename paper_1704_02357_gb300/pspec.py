@@ -32,7 +32,8 @@ class Params(C.Structure):
     _fields_ = [("nmesh", C.c_int32), ("window", C.c_int32), ("interlaced", C.c_int32),
                 ("compensate", C.c_int32), ("precision", C.c_int32), ("ell_max", C.c_int32),
                 ("box_size", C.c_double), ("box_corner", C.c_double * 3), ("observer", C.c_double * 3),
-                ("P0", C.c_double), ("nbar", C.c_double), ("max_group_bytes", C.c_int64)]
+                ("P0", C.c_double), ("nbar", C.c_double), ("max_group_bytes", C.c_int64),
+                ("max_particles", C.c_int64)]
 
 
 class Catalog(C.Structure):
@@ -141,7 +142,7 @@ class Estimator:
 
     def __init__(self, nmesh: int, box_size: float, box_corner, observer=(0.0, 0.0, 0.0), window="cic",
                  interlaced=False, compensate=True, precision="fp32", ell_max=4, P0=0.0, nbar=0.0,
-                 max_group_bytes=0, max_kbins=512, device=None, stream=None):
+                 max_group_bytes=0, max_kbins=512, max_particles=0, device=None, stream=None):
         import torch
         lib = load()
         self.device = torch.device(device if device is not None else "cuda", )
@@ -151,7 +152,7 @@ class Estimator:
         self.params = Params(int(nmesh), WINDOWS[window], int(bool(interlaced)), int(bool(compensate)),
                              PRECISIONS[precision], int(ell_max), float(box_size),
                              (C.c_double * 3)(*box_corner), (C.c_double * 3)(*observer), float(P0), float(nbar),
-                             int(max_group_bytes))
+                             int(max_group_bytes), int(max_particles))
         self.max_kbins = int(max_kbins)
         nbytes = C.c_int64(0)
         with torch.cuda.device(self.device):
