@@ -82,6 +82,8 @@ typedef struct {
   int64_t max_group_bytes; /* cap on the per-group spectrum buffers; 0 = one whole multipole */
   int64_t max_particles;   /* data + randoms the tile-binned paint is sized for (FP32 meshes);
                               0, a larger catalog pair or FP64 meshes use direct atomic painting */
+  int32_t cache_randoms;   /* 0/1: reserve meshes for pspec_set_randoms / pspec_run_batch */
+  int32_t reserved;        /* 0 */
 } pspec_params;
 
 typedef struct {
@@ -139,6 +141,25 @@ pspec_status pspec_multipoles_device(void* ctx, const int32_t* ells, int32_t n_e
  * Enqueued on `stream` without synchronising. */
 pspec_status pspec_wedges(const double* P, const int32_t* ells, int32_t n_ells, int32_t n_kbins,
                           const double* mu_edges, int32_t n_mu, double* out, void* stream);
+
+/* Batched mocks sharing one randoms catalog (the batching pattern of the mock campaigns
+ * that motivate the method, Sec. 1 and Sec. 5). Needs a context created with cache_randoms = 1.
+ * pspec_set_randoms paints the randoms once (unscaled) into cached meshes and keeps their
+ * sums (W_r, S_r, I_r). pspec_run_batch then computes, for each of the n_mocks data catalogs
+ * (host array of descriptors; device pointers inside; n_mocks <= PSPEC_MAX_BATCH), exactly
+ * what pspec_paint + pspec_multipoles would give with those randoms: the data are painted,
+ * mesh = data - alpha * randoms is formed on the device, and the multipoles are computed.
+ * Outputs (device): P_all[mock][i][b] (n_mocks x n_ells x n_kbins), sums_all[mock] =
+ * {alpha, I, S, W_d} (nullable), k_mean and n_modes (n_kbins each; the same for every mock).
+ * With use_graph = 1 one mock's launch sequence is captured once as a CUDA graph (reused
+ * while ells, k_edges and the paint path stay the same) and replayed per mock; the kernels
+ * read the current mock from a device table and advance a device counter, so the host only
+ * launches the graph. Enqueued on the context's stream; returns without synchronising. */
+#define PSPEC_MAX_BATCH 4096
+pspec_status pspec_set_randoms(void* ctx, const pspec_catalog* randoms);
+pspec_status pspec_run_batch(void* ctx, const pspec_catalog* mocks, int32_t n_mocks, const int32_t* ells,
+                             int32_t n_ells, const double* k_edges, int32_t n_kbins, double* P_all,
+                             double* sums_all, double* k_mean, double* n_modes, int32_t use_graph);
 
 /* Catalog sums without any device allocation. The paper has no counterpart: this exists
  * for callers that cannot call cudaMalloc (code that runs while a CUDA graph is being

@@ -43,11 +43,26 @@ __device__ __forceinline__ double fkp_w(const PaintArgs& a, double nb) {
   return a.nbar ? (a.P0 > 0.0 ? 1.0 / (1.0 + nb * a.P0) : 1.0) : a.wf_default;
 }
 
+// Catalog fields from the device descriptor of the current mock, when the arguments carry one.
+__device__ __forceinline__ PaintArgs resolve(const PaintArgs& in) {
+  PaintArgs a = in;
+  if (a.dc) {
+    const DevCat d = a.dc[*a.cur];
+    a.pos = d.pos;
+    a.weight = d.weight;
+    a.nbar = d.nbar;
+    a.count = d.count;
+    a.pos_f32 = d.pos_f32;
+  }
+  return a;
+}
+
 // ------------------------------------------------------------------ a1: weighted catalogs
 // Per-block partials: [0] sum w_c, [1] sum v^2 (v = w_c w_fkp), [2] sum nbar w_c w_fkp^2.
 // Invalid particles are left out here and counted by the paint kernel.
-__global__ void __launch_bounds__(kSumThreads) k_catalog_partials(PaintArgs a, double* out) {
+__global__ void __launch_bounds__(kSumThreads) k_catalog_partials(PaintArgs a_in, double* out) {
   __shared__ double red[kSumThreads / 32];
+  const PaintArgs a = resolve(a_in);
   double s0 = 0.0, s1 = 0.0, s2 = 0.0;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.count;
        p += (int64_t)gridDim.x * blockDim.x) {
@@ -223,9 +238,10 @@ __device__ __forceinline__ void scatter(T* __restrict__ m, int N, const int (&ix
 }
 
 template <typename T, int WIN, bool INTER>
-__global__ void __launch_bounds__(256) k_paint(PaintArgs a, int is_randoms, double* __restrict__ derived,
+__global__ void __launch_bounds__(256) k_paint(PaintArgs a_in, int is_randoms, double* __restrict__ derived,
                                                T* __restrict__ m1, T* __restrict__ m2, int N) {
-  const double sign = is_randoms ? -derived[D_ALPHA] : 1.0;
+  const PaintArgs a = resolve(a_in);
+  const double sign = is_randoms == 1 ? -derived[D_ALPHA] : 1.0;
   const bool uniform = (a.weight == nullptr) && (a.nbar == nullptr);
   const T v_uniform = (T)(sign * a.wf_default);
   const double lim = (double)N;
@@ -288,8 +304,8 @@ __global__ void __launch_bounds__(256) k_paint(PaintArgs a, int is_randoms, doub
 template <typename T>
 void launch_paint(const PaintArgs& a, int window, int interlaced, int is_randoms, double* derived, T* mesh1, T* mesh2,
                   int N, int nblocks, cudaStream_t s) {
-  if (a.count <= 0) return;
-  const int64_t need = (a.count + 255) / 256;
+  if (!a.dc && a.count <= 0) return;
+  const int64_t need = a.dc ? nblocks : (a.count + 255) / 256;
   const int nb = (int)(need < nblocks ? need : nblocks);
   if (window == PSPEC_WINDOW_CIC) {
     if (interlaced)
@@ -320,9 +336,10 @@ constexpr int kPS3 = kPS * kPS * kPS;
 constexpr unsigned kNoTile = 0xffffffffu;
 
 template <int WIN>
-__global__ void __launch_bounds__(256) k_ptile_prep(PaintArgs a, int is_randoms, double* __restrict__ derived,
+__global__ void __launch_bounds__(256) k_ptile_prep(PaintArgs a_in, int is_randoms, double* __restrict__ derived,
                                                     TileArgs ta, int64_t offset, int N) {
-  const double sign = is_randoms ? -derived[D_ALPHA] : 1.0;
+  const PaintArgs a = resolve(a_in);
+  const double sign = is_randoms == 1 ? -derived[D_ALPHA] : 1.0;
   const bool uniform = (a.weight == nullptr) && (a.nbar == nullptr);
   const float v_uniform = (float)(sign * a.wf_default);
   const double lim = (double)N;
@@ -395,7 +412,8 @@ __global__ void __launch_bounds__(1024) k_ptile_scan(TileArgs ta, int ntiles) {
   }
 }
 
-__global__ void __launch_bounds__(256) k_ptile_scatter(TileArgs ta, int64_t total) {
+__global__ void __launch_bounds__(256) k_ptile_scatter(TileArgs ta, int64_t total, const DevCat* dc, const int* cur) {
+  if (dc) total = dc[*cur].count;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += (int64_t)gridDim.x * blockDim.x) {
     const unsigned t = ta.tile_of[p];
     if (t == kNoTile) continue;
@@ -495,8 +513,8 @@ __global__ void __launch_bounds__(256) k_ptile_paint(TileArgs ta, float* __restr
 
 void launch_ptile_prep(const PaintArgs& a, int window, int is_randoms, double* derived, const TileArgs& ta,
                        int64_t offset, int N, int nblocks, cudaStream_t s) {
-  if (a.count <= 0) return;
-  const int64_t need = (a.count + 255) / 256;
+  if (!a.dc && a.count <= 0) return;
+  const int64_t need = a.dc ? nblocks : (a.count + 255) / 256;
   const int nb = (int)(need < nblocks ? need : nblocks);
   if (window == PSPEC_WINDOW_CIC)
     k_ptile_prep<PSPEC_WINDOW_CIC><<<nb, 256, 0, s>>>(a, is_randoms, derived, ta, offset, N);
@@ -506,11 +524,12 @@ void launch_ptile_prep(const PaintArgs& a, int window, int is_randoms, double* d
 
 void launch_ptile_scan(const TileArgs& ta, int ntiles, cudaStream_t s) { k_ptile_scan<<<1, 1024, 0, s>>>(ta, ntiles); }
 
-void launch_ptile_scatter(const TileArgs& ta, int64_t total, int nblocks, cudaStream_t s) {
-  if (total <= 0) return;
-  const int64_t need = (total + 255) / 256;
+void launch_ptile_scatter(const TileArgs& ta, int64_t total, const DevCat* dc, const int* cur, int nblocks,
+                          cudaStream_t s) {
+  if (!dc && total <= 0) return;
+  const int64_t need = dc ? nblocks : (total + 255) / 256;
   const int nb = (int)(need < nblocks ? need : nblocks);
-  k_ptile_scatter<<<nb, 256, 0, s>>>(ta, total);
+  k_ptile_scatter<<<nb, 256, 0, s>>>(ta, total, dc, cur);
 }
 
 template <typename K> static void set_smem_attr(K kernel, size_t bytes) {
@@ -536,6 +555,85 @@ void launch_ptile_paint(const TileArgs& ta, int window, int interlaced, float* m
     }
   }
 }
+
+// ------------------------------------------------------------------ batched mocks
+// rsums = (W_r, S_r, I_r) of the cached randoms.
+__global__ void k_randoms_sums(const double* pr, int nbr, double* rsums) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  Neu wr, sr, ir;
+  for (int b = 0; b < nbr; b++) {
+    wr.add(pr[b * kSumVals + 0]);
+    sr.add(pr[b * kSumVals + 1]);
+    ir.add(pr[b * kSumVals + 2]);
+  }
+  rsums[0] = wr.val();
+  rsums[1] = sr.val();
+  rsums[2] = ir.val();
+}
+
+__global__ void k_catalog_final_cached(const double* pd, int nbd, const double* rsums, double* d) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  Neu wd, sd;
+  for (int b = 0; b < nbd; b++) {
+    wd.add(pd[b * kSumVals + 0]);
+    sd.add(pd[b * kSumVals + 1]);
+  }
+  const double Wr = rsums[0], Sr = rsums[1], Ir = rsums[2];
+  const double alpha = wd.val() / Wr;
+  d[D_WD] = wd.val();
+  d[D_WR] = Wr;
+  d[D_ALPHA] = alpha;
+  d[D_I] = alpha * Ir;
+  d[D_S] = sd.val() + alpha * alpha * Sr;
+  d[D_NONFINITE] = 0.0;
+  d[D_WRAPPED] = 0.0;
+  d[D_SD] = sd.val();
+  d[D_SR] = Sr;
+  d[D_IR] = Ir;
+}
+
+template <typename T>
+__global__ void k_axpy_randoms(T* __restrict__ m, const T* __restrict__ r, int64_t n, const double* __restrict__ d) {
+  const T a = (T)d[D_ALPHA];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    m[i] -= a * r[i];
+}
+
+__global__ void k_batch_outputs(const double* __restrict__ P, int n, const double* __restrict__ d,
+                                const int* __restrict__ cur, double* P_all, double* sums_all) {
+  const int c = *cur;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    P_all[(int64_t)c * n + i] = P[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0 && sums_all) {
+    sums_all[4 * c + 0] = d[D_ALPHA];
+    sums_all[4 * c + 1] = d[D_I];
+    sums_all[4 * c + 2] = d[D_S];
+    sums_all[4 * c + 3] = d[D_WD];
+  }
+}
+
+__global__ void k_advance(int* cur) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *cur += 1;
+}
+
+void launch_randoms_sums(const double* part_r, int nb_r, double* rsums, cudaStream_t s) {
+  k_randoms_sums<<<1, 32, 0, s>>>(part_r, nb_r, rsums);
+}
+void launch_catalog_final_cached(const double* part_d, int nb_d, const double* rsums, double* derived,
+                                 cudaStream_t s) {
+  k_catalog_final_cached<<<1, 32, 0, s>>>(part_d, nb_d, rsums, derived);
+}
+void launch_axpy_randoms(float* mesh, const float* rmesh, int64_t n, const double* derived, cudaStream_t s) {
+  k_axpy_randoms<float><<<2048, 256, 0, s>>>(mesh, rmesh, n, derived);
+}
+void launch_axpy_randoms(double* mesh, const double* rmesh, int64_t n, const double* derived, cudaStream_t s) {
+  k_axpy_randoms<double><<<2048, 256, 0, s>>>(mesh, rmesh, n, derived);
+}
+void launch_batch_outputs(const double* P, int n_ells, int nk, const double* derived, const int* cur, double* P_all,
+                          double* sums_all, cudaStream_t s) {
+  k_batch_outputs<<<(n_ells * nk + 127) / 128, 128, 0, s>>>(P, n_ells * nk, derived, cur, P_all, sums_all);
+}
+void launch_advance(int* cur, cudaStream_t s) { k_advance<<<1, 32, 0, s>>>(cur); }
 
 // ------------------------------------------------------------------ a6: finalise
 struct EllList {

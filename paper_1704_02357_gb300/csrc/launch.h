@@ -19,6 +19,17 @@ enum { SLOT_P0 = 0, SLOT_ELL0 = 1 };
 enum { D_WD = 0, D_WR, D_ALPHA, D_I, D_S, D_NONFINITE, D_WRAPPED, D_SD, D_SR, D_IR, D_COUNT = 16 };
 constexpr int kSumVals = 4;  // per-block partial: w_c, v^2, nbar w_c w_fkp^2, spare
 
+// A catalog as a device-side descriptor (batched mocks: the kernels of one captured graph
+// read the current mock's catalog from a table indexed by a device counter).
+struct DevCat {
+  const void* pos;
+  const double* weight;
+  const double* nbar;
+  long long count;
+  int pos_f32;
+  int pad;
+};
+
 struct PaintArgs {
   const void* pos;
   int pos_f32;
@@ -30,6 +41,8 @@ struct PaintArgs {
   double P0;
   double nbar_default;
   double wf_default;    // FKP weight for nbar_default
+  const DevCat* dc;     // when set, pos/weight/nbar/count come from dc[*cur]
+  const int* cur;
 };
 
 struct BinArgs {
@@ -45,7 +58,19 @@ void launch_catalog_final(const double* part_d, int nb_d, const double* part_r, 
                           cudaStream_t s);
 void launch_derive_uniform(int64_t n_d, int64_t n_r, double wf, double nbar, double* derived, cudaStream_t s);
 
+// Batched mocks: randoms sums kept from pspec_set_randoms (W_r, S_r, I_r), the data sums of
+// the current mock combined with them; mesh -= alpha * cached randoms mesh; counter += 1.
+void launch_catalog_final_cached(const double* part_d, int nb_d, const double* rsums, double* derived,
+                                 cudaStream_t s);
+void launch_randoms_sums(const double* part_r, int nb_r, double* rsums, cudaStream_t s);
+void launch_axpy_randoms(float* mesh, const float* rmesh, int64_t n, const double* derived, cudaStream_t s);
+void launch_axpy_randoms(double* mesh, const double* rmesh, int64_t n, const double* derived, cudaStream_t s);
+void launch_batch_outputs(const double* P, int n_ells, int nk, const double* derived, const int* cur, double* P_all,
+                          double* sums_all, cudaStream_t s);
+void launch_advance(int* cur, cudaStream_t s);
+
 // a2: scatter-add painting; counts invalid and out-of-box particles into derived.
+// is_randoms: 0 data (+v), 1 randoms (-alpha v), 2 randoms unscaled (+v, cached meshes).
 template <typename T>
 void launch_paint(const PaintArgs& a, int window, int interlaced, int is_randoms, double* derived, T* mesh1,
                   T* mesh2, int N, int nblocks, cudaStream_t s);
@@ -64,7 +89,8 @@ struct TileArgs {
 void launch_ptile_prep(const PaintArgs& a, int window, int is_randoms, double* derived, const TileArgs& ta,
                        int64_t offset, int N, int nblocks, cudaStream_t s);
 void launch_ptile_scan(const TileArgs& ta, int ntiles, cudaStream_t s);
-void launch_ptile_scatter(const TileArgs& ta, int64_t total, int nblocks, cudaStream_t s);
+void launch_ptile_scatter(const TileArgs& ta, int64_t total, const DevCat* dc, const int* cur, int nblocks,
+                          cudaStream_t s);
 void launch_ptile_paint(const TileArgs& ta, int window, int interlaced, float* m1, float* m2, int N, cudaStream_t s);
 
 // Transform passes, one table of launchers per supported mesh side N (pass_*.cu).

@@ -58,6 +58,8 @@ PaintArgs args_for(const pspec_params* p, const pspec_catalog* c) {
   a.P0 = p->P0;
   a.nbar_default = p->nbar;
   a.wf_default = p->P0 > 0 ? 1.0 / (1.0 + p->nbar * p->P0) : 1.0;
+  a.dc = nullptr;
+  a.cur = nullptr;
   return a;
 }
 

@@ -56,6 +56,8 @@ struct Plan {
       o_psort, total;
   int64_t max_particles;  // capacity of the tile-binned paint (0: direct painting only)
   int ntiles;
+  bool cache_randoms;
+  size_t o_rmesh1, o_rmesh2, o_rsums, o_desc, o_cur;
 };
 
 pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl, std::string* why) {
@@ -145,6 +147,14 @@ pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl,
     pl->o_ptile = take((size_t)pl->max_particles * sizeof(unsigned));
     pl->o_psort = take((size_t)pl->max_particles * 16);
   }
+  pl->cache_randoms = p->cache_randoms != 0;
+  if (pl->cache_randoms) {
+    pl->o_rmesh1 = take(pl->Sr);
+    pl->o_rmesh2 = p->interlaced ? take(pl->Sr) : 0;
+    pl->o_rsums = take(4 * sizeof(double));
+    pl->o_desc = take((size_t)PSPEC_MAX_BATCH * sizeof(DevCat));
+    pl->o_cur = take(sizeof(int));
+  }
   pl->total = o;
   return PSPEC_OK;
 }
@@ -159,7 +169,17 @@ struct Ctx {
   int nsm = 0;
   Plan pl;
   bool painted = false;
+  bool randoms_set = false;
   std::vector<double> edges;
+  // captured per-mock graph and what it was captured for
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t cap_stream = nullptr;  // graphs are captured and replayed here (never the legacy stream)
+  std::vector<int32_t> graph_ells;
+  std::vector<double> graph_edges;
+  int graph_binned = -1;
+  int64_t graph_kernels = 0;
+  std::vector<DevCat> desc_host;
+  pspec_catalog batch_proto{};  // dtype of the mocks' positions (pointers come from the table)
   std::string err;
   int64_t launches = 0;
   int64_t transforms_last = 0;
@@ -342,6 +362,8 @@ PaintArgs paint_args(Ctx* c, const pspec_catalog* cat) {
   a.P0 = c->p.P0;
   a.nbar_default = c->p.nbar;
   a.wf_default = fkp(c->p.nbar, c->p.P0);
+  a.dc = nullptr;
+  a.cur = nullptr;
   return a;
 }
 
@@ -400,7 +422,7 @@ pspec_status do_paint(Ctx* c, const pspec_catalog* d, const pspec_catalog* r) {
       launch_ptile_prep(ar, c->p.window, 1, der, ta, d->count, N, nb, c->stream);
     }));
     TRY(run(c, PSPEC_K_PAINT, 0.0, [&] { launch_ptile_scan(ta, pl.ntiles, c->stream); }));
-    TRY(run(c, PSPEC_K_PAINT, 0.0, [&] { launch_ptile_scatter(ta, total, nb, c->stream); }));
+    TRY(run(c, PSPEC_K_PAINT, 0.0, [&] { launch_ptile_scatter(ta, total, nullptr, nullptr, nb, c->stream); }));
     TRY(run(c, PSPEC_K_PAINT, nmesh * pl.Sr, [&] {
       launch_ptile_paint(ta, c->p.window, c->p.interlaced, f1, f2, N, c->stream);
     }));
@@ -517,6 +539,94 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
   return PSPEC_OK;
 }
 
+TileArgs tile_args(Ctx* c) {
+  const Plan& pl = c->pl;
+  TileArgs ta;
+  ta.cnt = c->at<unsigned>(pl.o_tcnt);
+  ta.off = c->at<unsigned>(pl.o_toff);
+  ta.cursor = c->at<unsigned>(pl.o_tcur);
+  ta.rec = c->at<uint4>(pl.o_prec);
+  ta.tile_of = c->at<unsigned>(pl.o_ptile);
+  ta.sorted = c->at<uint4>(pl.o_psort);
+  return ta;
+}
+
+// Paint `a` (a data catalog, or randoms with is_randoms = 2) into m1/m2 (zeroed here):
+// tile-binned when `binned`, else direct atomics. `max_count` bounds the particles.
+template <typename T>
+pspec_status paint_one(Ctx* c, const PaintArgs& a, int is_randoms, bool binned, int64_t max_count, T* m1, T* m2) {
+  const Plan& pl = c->pl;
+  const int N = pl.g.N;
+  const int nb = 16 * c->nsm;
+  double* der = c->at<double>(pl.o_derived);
+  cudaError_t e = cudaMemsetAsync(m1, 0, pl.Sr, c->stream);
+  if (e == cudaSuccess && m2) e = cudaMemsetAsync(m2, 0, pl.Sr, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "mesh clear");
+  const double nmesh = c->p.interlaced ? 2.0 : 1.0;
+  const double pbytes = (a.pos_f32 ? 12.0 : 24.0) * (double)max_count;
+  if (binned && sizeof(T) == 4) {
+    TileArgs ta = tile_args(c);
+    e = cudaMemsetAsync(ta.cnt, 0, (size_t)pl.ntiles * sizeof(unsigned), c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tile counts clear");
+    TRY(run(c, PSPEC_K_PAINT, pbytes, [&] { launch_ptile_prep(a, c->p.window, is_randoms, der, ta, 0, N, nb, c->stream); }));
+    TRY(run(c, PSPEC_K_PAINT, 0.0, [&] { launch_ptile_scan(ta, pl.ntiles, c->stream); }));
+    TRY(run(c, PSPEC_K_PAINT, 0.0, [&] { launch_ptile_scatter(ta, a.count, a.dc, a.cur, nb, c->stream); }));
+    TRY(run(c, PSPEC_K_PAINT, nmesh * pl.Sr, [&] {
+      launch_ptile_paint(ta, c->p.window, c->p.interlaced, reinterpret_cast<float*>(m1), reinterpret_cast<float*>(m2),
+                         N, c->stream);
+    }));
+  } else {
+    TRY(run(c, PSPEC_K_PAINT, pbytes + nmesh * pl.Sr, [&] {
+      launch_paint<T>(a, c->p.window, c->p.interlaced, is_randoms, der, m1, m2, N, nb, c->stream);
+    }));
+  }
+  return PSPEC_OK;
+}
+
+template <typename T>
+pspec_status do_set_randoms(Ctx* c, const pspec_catalog* r) {
+  const Plan& pl = c->pl;
+  PaintArgs ar = paint_args(c, r);
+  double* part = c->at<double>(pl.o_sums) + (size_t)pl.nblk_sum * kSumVals;
+  TRY(run(c, PSPEC_K_SUMS, cat_bytes(r), [&] { launch_catalog_partials(ar, part, pl.nblk_sum, c->stream); }));
+  TRY(run(c, PSPEC_K_SUMS, 0.0, [&] { launch_randoms_sums(part, pl.nblk_sum, c->at<double>(pl.o_rsums), c->stream); }));
+  T* r1 = c->at<T>(pl.o_rmesh1);
+  T* r2 = c->p.interlaced ? c->at<T>(pl.o_rmesh2) : nullptr;
+  const bool binned = pl.max_particles >= r->count;
+  TRY(paint_one<T>(c, ar, 2, binned, r->count, r1, r2));
+  return PSPEC_OK;
+}
+
+// One mock of a batch: sums, paint, mesh -= alpha * randoms, multipoles, outputs, counter.
+template <typename T>
+pspec_status enqueue_mock(Ctx* c, bool binned, int64_t max_count, const int32_t* ells, int n_ells, int nk,
+                          double* P_all, double* sums_all) {
+  const Plan& pl = c->pl;
+  PaintArgs a = paint_args(c, &c->batch_proto);
+  a.dc = c->at<DevCat>(pl.o_desc);
+  a.cur = c->at<int>(pl.o_cur);
+  double* part = c->at<double>(pl.o_sums);
+  double* der = c->at<double>(pl.o_derived);
+  TRY(run(c, PSPEC_K_SUMS, 0.0, [&] { launch_catalog_partials(a, part, pl.nblk_sum, c->stream); }));
+  TRY(run(c, PSPEC_K_SUMS, 0.0, [&] {
+    launch_catalog_final_cached(part, pl.nblk_sum, c->at<double>(pl.o_rsums), der, c->stream);
+  }));
+  T* m1 = c->at<T>(pl.o_mesh1);
+  T* m2 = c->p.interlaced ? c->at<T>(pl.o_mesh2) : nullptr;
+  TRY(paint_one<T>(c, a, 0, binned, max_count, m1, m2));
+  const int64_t n = (int64_t)pl.g.N * pl.g.N * pl.g.N;
+  TRY(run(c, PSPEC_K_OTHER, 3.0 * pl.Sr, [&] { launch_axpy_randoms(m1, c->at<T>(pl.o_rmesh1), n, der, c->stream); }));
+  if (m2)
+    TRY(run(c, PSPEC_K_OTHER, 3.0 * pl.Sr, [&] { launch_axpy_randoms(m2, c->at<T>(pl.o_rmesh2), n, der, c->stream); }));
+  double* out = c->at<double>(pl.o_out);
+  TRY(do_multipoles<T>(c, ells, n_ells, nk, out + 2 * (size_t)nk, out, out + nk));
+  TRY(run(c, PSPEC_K_OTHER, 0.0, [&] {
+    launch_batch_outputs(out + 2 * (size_t)nk, n_ells, nk, der, a.cur, P_all, sums_all, c->stream);
+  }));
+  TRY(run(c, PSPEC_K_OTHER, 0.0, [&] { launch_advance(c->at<int>(pl.o_cur), c->stream); }));
+  return PSPEC_OK;
+}
+
 pspec_status check_ells_edges(Ctx* c, const int32_t* ells, int n_ells, const double* k_edges, int nk) {
   if (!ells || n_ells < 1 || n_ells > kMaxElls) { c->err = "need 1..9 multipoles"; return PSPEC_EINVAL; }
   for (int i = 0; i < n_ells; i++) {
@@ -605,6 +715,8 @@ pspec_status pspec_destroy(void* ctx) {
     cudaEventDestroy(r.b);
   }
   for (auto ev : c->pool) cudaEventDestroy(ev);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
   return PSPEC_OK;
 }
@@ -669,6 +781,137 @@ pspec_status pspec_multipoles_device(void* ctx, const int32_t* ells, int32_t n_e
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!P_dev || !k_mean_dev || !n_modes_dev) { c->err = "output pointers are NULL"; return PSPEC_EINVAL; }
   return multipoles_common(c, ells, n_ells, k_edges, n_kbins, P_dev, k_mean_dev, n_modes_dev);
+}
+
+pspec_status pspec_set_randoms(void* ctx, const pspec_catalog* randoms) {
+  if (!ctx) return PSPEC_EINVAL;
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c->pl.cache_randoms) { c->err = "context was created without cache_randoms"; return PSPEC_ESTATE; }
+  TRY(check_catalog(c, randoms, "randoms", true));
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  pspec_status st = c->p.precision == PSPEC_FP64 ? do_set_randoms<double>(c, randoms) : do_set_randoms<float>(c, randoms);
+  if (st != PSPEC_OK) return st;
+  c->randoms_set = true;
+  return PSPEC_OK;
+}
+
+pspec_status pspec_run_batch(void* ctx, const pspec_catalog* mocks, int32_t n_mocks, const int32_t* ells,
+                             int32_t n_ells, const double* k_edges, int32_t n_kbins, double* P_all, double* sums_all,
+                             double* k_mean, double* n_modes, int32_t use_graph) {
+  if (!ctx) return PSPEC_EINVAL;
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c->pl.cache_randoms || !c->randoms_set) { c->err = "pspec_set_randoms must come first"; return PSPEC_ESTATE; }
+  if (!mocks || n_mocks < 1 || n_mocks > PSPEC_MAX_BATCH) { c->err = "n_mocks out of range"; return PSPEC_EINVAL; }
+  if (!P_all || !k_mean || !n_modes) { c->err = "output pointers are NULL"; return PSPEC_EINVAL; }
+  int64_t max_count = 0;
+  for (int i = 0; i < n_mocks; i++) {
+    TRY(check_catalog(c, &mocks[i], "mock", false));
+    if (mocks[i].pos_dtype != mocks[0].pos_dtype) { c->err = "mocks must share one position dtype"; return PSPEC_EINVAL; }
+    max_count = std::max(max_count, mocks[i].count);
+  }
+  c->painted = true;  // the meshes are produced inside the batch sequence
+  TRY(check_ells_edges(c, ells, n_ells, k_edges, n_kbins));
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  TRY(upload_bins(c, k_edges, n_kbins));  // synchronous, so before any capture
+  const Plan& pl = c->pl;
+  c->desc_host.resize(n_mocks);
+  for (int i = 0; i < n_mocks; i++) {
+    DevCat d;
+    d.pos = mocks[i].pos;
+    d.weight = mocks[i].weight;
+    d.nbar = mocks[i].nbar;
+    d.count = mocks[i].count;
+    d.pos_f32 = mocks[i].pos_dtype == PSPEC_POS_F32;
+    d.pad = 0;
+    c->desc_host[i] = d;
+  }
+  c->batch_proto = mocks[0];
+  e = cudaMemcpyAsync(c->at<DevCat>(pl.o_desc), c->desc_host.data(), n_mocks * sizeof(DevCat), cudaMemcpyHostToDevice,
+                      c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->at<int>(pl.o_cur), 0, sizeof(int), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "batch table upload");
+  const bool binned = pl.max_particles >= max_count && c->p.precision == PSPEC_FP32;
+  const bool f64 = c->p.precision == PSPEC_FP64;
+  auto one = [&]() {
+    return f64 ? enqueue_mock<double>(c, binned, max_count, ells, n_ells, n_kbins, P_all, sums_all)
+               : enqueue_mock<float>(c, binned, max_count, ells, n_ells, n_kbins, P_all, sums_all);
+  };
+  if (!use_graph) {
+    for (int i = 0; i < n_mocks; i++) TRY(one());
+  } else {
+    // capture and replay on a private stream ordered after, and before, the caller's stream
+    if (!c->cap_stream) {
+      e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return cuda_fail(c, e, "capture stream");
+    }
+    cudaStream_t user = c->stream;
+    cudaEvent_t ev_in = take_event(c), ev_out = take_event(c);
+    e = cudaEventRecord(ev_in, user);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->cap_stream, ev_in, 0);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream ordering");
+    c->stream = c->cap_stream;
+    struct Restore {
+      Ctx* c;
+      cudaStream_t user;
+      cudaEvent_t ev_in, ev_out;
+      ~Restore() {
+        cudaEventRecord(ev_out, c->stream);
+        c->stream = user;
+        cudaStreamWaitEvent(user, ev_out, 0);
+        c->pool.push_back(ev_in);
+        c->pool.push_back(ev_out);
+      }
+    } restore{c, user, ev_in, ev_out};
+    std::vector<int32_t> ev(ells, ells + n_ells);
+    std::vector<double> ed(k_edges, k_edges + n_kbins + 1);
+    if (!c->graph || ev != c->graph_ells || ed != c->graph_edges || c->graph_binned != (int)binned) {
+      if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+      }
+      const bool prof = c->prof;
+      c->prof = false;
+      const int64_t l0 = c->launches;
+      e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed);
+      if (e != cudaSuccess) {
+        c->prof = prof;
+        return cuda_fail(c, e, "begin capture");
+      }
+      pspec_status st = one();
+      cudaGraph_t g = nullptr;
+      cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+      c->prof = prof;
+      if (st != PSPEC_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+      }
+      if (e2 != cudaSuccess) return cuda_fail(c, e2, "end capture");
+      e2 = cudaGraphInstantiate(&c->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e2 != cudaSuccess) {
+        c->graph = nullptr;
+        return cuda_fail(c, e2, "graph instantiate");
+      }
+      c->graph_kernels = c->launches - l0;
+      c->launches = l0;
+      c->graph_ells = ev;
+      c->graph_edges = ed;
+      c->graph_binned = (int)binned;
+    }
+    for (int i = 0; i < n_mocks; i++) {
+      e = cudaGraphLaunch(c->graph, c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
+    }
+    c->launches += c->graph_kernels * n_mocks;
+  }
+  double* out = c->at<double>(pl.o_out);
+  e = cudaMemcpyAsync(k_mean, out, n_kbins * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(n_modes, out + n_kbins, n_kbins * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "batch outputs");
+  return PSPEC_OK;
 }
 
 pspec_status pspec_wedges(const double* P, const int32_t* ells, int32_t n_ells, int32_t n_kbins, const double* mu_edges,

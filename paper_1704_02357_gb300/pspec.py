@@ -33,7 +33,7 @@ class Params(C.Structure):
                 ("compensate", C.c_int32), ("precision", C.c_int32), ("ell_max", C.c_int32),
                 ("box_size", C.c_double), ("box_corner", C.c_double * 3), ("observer", C.c_double * 3),
                 ("P0", C.c_double), ("nbar", C.c_double), ("max_group_bytes", C.c_int64),
-                ("max_particles", C.c_int64)]
+                ("max_particles", C.c_int64), ("cache_randoms", C.c_int32), ("reserved", C.c_int32)]
 
 
 class Catalog(C.Structure):
@@ -79,6 +79,10 @@ SIGNATURES = [
     ("pspec_strerror", C.c_char_p, [C.c_int32]),
     ("pspec_last_error", C.c_char_p, [C.c_void_p]),
     ("pspec_version", C.c_char_p, []),
+    ("pspec_set_randoms", C.c_int32, [C.c_void_p, C.POINTER(Catalog)]),
+    ("pspec_run_batch", C.c_int32, [C.c_void_p, C.POINTER(Catalog), C.c_int32, C.POINTER(C.c_int32), C.c_int32,
+                                    C.POINTER(C.c_double), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_int32]),
     ("pspec_catalog_sums_noalloc", C.c_int32, [C.POINTER(Params), C.POINTER(Catalog), C.POINTER(Catalog), C.c_int32,
                                                C.c_void_p, C.c_void_p]),
 ]
@@ -142,7 +146,8 @@ class Estimator:
 
     def __init__(self, nmesh: int, box_size: float, box_corner, observer=(0.0, 0.0, 0.0), window="cic",
                  interlaced=False, compensate=True, precision="fp32", ell_max=4, P0=0.0, nbar=0.0,
-                 max_group_bytes=0, max_kbins=512, max_particles=0, device=None, stream=None):
+                 max_group_bytes=0, max_kbins=512, max_particles=0, cache_randoms=False, device=None,
+                 stream=None):
         import torch
         lib = load()
         self.device = torch.device(device if device is not None else "cuda", )
@@ -152,7 +157,7 @@ class Estimator:
         self.params = Params(int(nmesh), WINDOWS[window], int(bool(interlaced)), int(bool(compensate)),
                              PRECISIONS[precision], int(ell_max), float(box_size),
                              (C.c_double * 3)(*box_corner), (C.c_double * 3)(*observer), float(P0), float(nbar),
-                             int(max_group_bytes), int(max_particles))
+                             int(max_group_bytes), int(max_particles), int(bool(cache_randoms)), 0)
         self.max_kbins = int(max_kbins)
         nbytes = C.c_int64(0)
         with torch.cuda.device(self.device):
@@ -204,6 +209,42 @@ class Estimator:
         _check(lib.pspec_multipoles_device(self._ctx, el, len(ells), edges.ctypes.data_as(C.POINTER(C.c_double)),
                                            len(edges) - 1, C.c_void_p(_ptr(P_out)), C.c_void_p(_ptr(kmean_out)),
                                            C.c_void_p(_ptr(nmodes_out))), self._ctx)
+
+    # ------------------------------------------------------------------ batched mocks
+    def set_randoms(self, pos, weight=None, nbar=None):
+        """Paint the shared randoms once into the cached meshes (needs cache_randoms=True)."""
+        keep = []
+        r = _catalog(pos, weight, nbar, self.device, keep)
+        self._rkeep = keep
+        _check(load().pspec_set_randoms(self._ctx, C.byref(r)), self._ctx)
+
+    def run_batch(self, mocks, ells: Sequence[int], k_edges, use_graph=True):
+        """Multipoles of every mock (list of (pos[, weight[, nbar]])) against the cached randoms.
+
+        Returns device tensors P (n_mocks, n_ells, nk), sums (n_mocks, 4: alpha, I, S, W_d),
+        k_mean (nk), n_modes (nk); enqueued on the context's stream.
+        """
+        import torch
+        ells = [int(e) for e in ells]
+        edges = np.ascontiguousarray(k_edges, dtype=np.float64)
+        nk = len(edges) - 1
+        keep = []
+        cats = []
+        for m in mocks:
+            m = m if isinstance(m, (tuple, list)) else (m,)
+            cats.append(_catalog(m[0], m[1] if len(m) > 1 else None, m[2] if len(m) > 2 else None, self.device, keep))
+        arr = (Catalog * len(cats))(*cats)
+        P = torch.empty((len(cats), len(ells), nk), dtype=torch.float64, device=self.device)
+        sums = torch.empty((len(cats), 4), dtype=torch.float64, device=self.device)
+        km = torch.empty(nk, dtype=torch.float64, device=self.device)
+        nm = torch.empty(nk, dtype=torch.float64, device=self.device)
+        el = (C.c_int32 * len(ells))(*ells)
+        _check(load().pspec_run_batch(self._ctx, arr, len(cats), el, len(ells),
+                                      edges.ctypes.data_as(C.POINTER(C.c_double)), nk, C.c_void_p(P.data_ptr()),
+                                      C.c_void_p(sums.data_ptr()), C.c_void_p(km.data_ptr()),
+                                      C.c_void_p(nm.data_ptr()), int(bool(use_graph))), self._ctx)
+        self._bkeep = keep
+        return {"P": P, "sums": sums, "k_mean": km, "n_modes": nm, "ells": ells}
 
     def plan_info(self) -> dict:
         info = PlanInfo()
