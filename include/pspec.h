@@ -180,6 +180,27 @@ pspec_status pspec_catalog_sums_noalloc(const pspec_params* p, const pspec_catal
                                         const pspec_catalog* randoms, int32_t nblocks, double* out,
                                         void* stream);
 
+/* Runtime knobs of a context and the autotuner that picks them (batching pattern: the
+ * transform tiles and the paint strategy are chosen by measurement).
+ *   paint_binned       1: tile-binned paint when the catalogs fit max_particles; 0: direct atomics
+ *   ylm_harmonics      harmonics per block of the Y_lm-weighted z pass (>= 1)
+ *   bin_blocks_per_sm  persistent blocks per SM of the combine/binning passes (0: occupancy limit)
+ *   tile_y             0: the compiled y-pass tile; 1: half as many columns per block
+ * pspec_autotune paints the given catalogs and times pspec_multipoles_device for candidate
+ * settings (reps timed runs each, CUDA events on the context's stream), keeps the fastest
+ * and returns it in *best. It synchronises the stream. */
+typedef struct {
+  int32_t paint_binned;
+  int32_t ylm_harmonics;
+  int32_t bin_blocks_per_sm;
+  int32_t tile_y;
+} pspec_tuning;
+pspec_status pspec_get_tuning(void* ctx, pspec_tuning* t);
+pspec_status pspec_set_tuning(void* ctx, const pspec_tuning* t);
+pspec_status pspec_autotune(void* ctx, const pspec_catalog* data, const pspec_catalog* randoms,
+                            const int32_t* ells, int32_t n_ells, const double* k_edges, int32_t n_kbins,
+                            int32_t reps, pspec_tuning* best);
+
 /* Plan facts for tests and reports. */
 typedef struct {
   int32_t nmesh, precision, ell_max;

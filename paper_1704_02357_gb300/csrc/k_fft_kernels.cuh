@@ -188,12 +188,12 @@ __global__ void __launch_bounds__(512) k_ylm_r2c_z(const T* __restrict__ f, cx<T
 
 // ------------------------------------------------------------------ pass y (in place)
 // Block: one (i, kz-tile) slab, TW columns x Tc threads (column fastest).
-template <typename T, int N, int DIR>
-__global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T>(Shape<N>::CT))
+template <typename T, int N, int DIR, int TW>
+__global__ void __launch_bounds__(TW * Shape<N>::Tc, min_blocks<T>(TW * Shape<N>::Tc))
     k_fft_y(cx<T>* __restrict__ data, int64_t spec_stride, const cx<T>* __restrict__ twf) {
   using C = cx<T>;
   using S = Shape<N>;
-  constexpr int NH = S::NH, E = S::E, Tc = S::Tc, TW = S::TW;
+  constexpr int NH = S::NH, E = S::E, Tc = S::Tc;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int c = threadIdx.x % TW, t = threadIdx.x / TW;
@@ -414,16 +414,24 @@ template <typename T, int N> struct Passes {
     k_ylm_r2c_z<T, N><<<N * N / rows, M * rows * S::Tz, smem, s>>>(f, out, stride, ell, h0, M, twh, twr, axis, rows,
                                                                     host_ytab<T>());
   }
-  static void fft_y(C* data, int64_t stride, int nspec, const C* twf, int dir, cudaStream_t s) {
-    const size_t smem = smem_col();
-    dim3 grid(N * (S::NH / S::TW), nspec);
+  // variant 0: TW columns per block; variant 1: TW/2 (half the threads and shared memory)
+  template <int TWV> static void fft_y_tw(C* data, int64_t stride, int nspec, const C* twf, int dir, cudaStream_t s) {
+    const size_t smem = (size_t)N * TWV * sizeof(C);
+    dim3 grid(N * (S::NH / TWV), nspec);
     if (dir < 0) {
-      set_smem(k_fft_y<T, N, -1>, smem);
-      k_fft_y<T, N, -1><<<grid, S::CT, smem, s>>>(data, stride, twf);
+      set_smem(k_fft_y<T, N, -1, TWV>, smem);
+      k_fft_y<T, N, -1, TWV><<<grid, TWV * S::Tc, smem, s>>>(data, stride, twf);
     } else {
-      set_smem(k_fft_y<T, N, 1>, smem);
-      k_fft_y<T, N, 1><<<grid, S::CT, smem, s>>>(data, stride, twf);
+      set_smem(k_fft_y<T, N, 1, TWV>, smem);
+      k_fft_y<T, N, 1, TWV><<<grid, TWV * S::Tc, smem, s>>>(data, stride, twf);
     }
+  }
+  static void fft_y(C* data, int64_t stride, int nspec, const C* twf, int dir, int variant, cudaStream_t s) {
+    constexpr int TW2 = S::TW > 1 ? S::TW / 2 : 1;
+    if (variant == 1 && S::TW > 1)
+      fft_y_tw<TW2>(data, stride, nspec, twf, dir, s);
+    else
+      fft_y_tw<S::TW>(data, stride, nspec, twf, dir, s);
   }
   static void fft_x(const C* in, C* out, const C* twf, int dir, cudaStream_t s) {
     const size_t smem = smem_col();

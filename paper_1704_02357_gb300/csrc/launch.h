@@ -120,7 +120,7 @@ template <typename T> struct PassTable {
   void (*c2r_z)(const cx<T>*, T*, const cx<T>*, const cx<T>*, T, cudaStream_t);
   void (*ylm_z)(const T*, cx<T>*, int64_t, int, int, int, const cx<T>*, const cx<T>*, const T*, int, cudaStream_t);
   size_t (*smem_ylm)(int, int);
-  void (*fft_y)(cx<T>*, int64_t, int, const cx<T>*, int, cudaStream_t);
+  void (*fft_y)(cx<T>*, int64_t, int, const cx<T>*, int, int, cudaStream_t);  // ..., dir, tile variant
   void (*fft_x)(const cx<T>*, cx<T>*, const cx<T>*, int, cudaStream_t);
   void (*combine_x)(const cx<T>*, cx<T>*, const cx<T>*, int, int, int, const cx<T>*, const T*, const BinArgs&, int,
                     cudaStream_t);

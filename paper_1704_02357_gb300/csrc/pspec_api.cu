@@ -180,6 +180,7 @@ struct Ctx {
   int64_t graph_kernels = 0;
   std::vector<DevCat> desc_host;
   pspec_catalog batch_proto{};  // dtype of the mocks' positions (pointers come from the table)
+  pspec_tuning tune{1, 64, 0, 0};
   std::string err;
   int64_t launches = 0;
   int64_t transforms_last = 0;
@@ -403,7 +404,7 @@ pspec_status do_paint(Ctx* c, const pspec_catalog* d, const pspec_catalog* r) {
   const int nb = 16 * c->nsm;
   const double nmesh = c->p.interlaced ? 2.0 : 1.0;
   const int64_t total = d->count + r->count;
-  if (sizeof(T) == 4 && pl.max_particles > 0 && total <= pl.max_particles) {
+  if (sizeof(T) == 4 && c->tune.paint_binned && pl.max_particles > 0 && total <= pl.max_particles) {
     TileArgs ta;
     ta.cnt = c->at<unsigned>(pl.o_tcnt);
     ta.off = c->at<unsigned>(pl.o_toff);
@@ -470,6 +471,11 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
   if (e != cudaSuccess) return cuda_fail(c, e, "bins clear");
   int64_t transforms = 0;
   double bytes = 0;
+  const int ntiles_x = N * (g.NH / PT->tw);
+  const int ctas_comb = c->tune.bin_blocks_per_sm > 0 ? std::min(ntiles_x, c->tune.bin_blocks_per_sm * c->nsm)
+                                                      : pl.ctas_comb;
+  const int ctas_bin = c->tune.bin_blocks_per_sm > 0 ? std::min(ntiles_x, c->tune.bin_blocks_per_sm * c->nsm)
+                                                     : pl.ctas_bin;
   auto acc = [&](double b) {
     bytes += b;
     return b;
@@ -477,24 +483,24 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
 
   // a3: F1 (and F2), combine + compensate -> F0 with the l = 0 sums; round trip -> f
   TRY(run(c, PSPEC_K_FFT_Z, acc(Sr + Sc), [&] { PT->r2c_z(m1, F0, twh, twr, s); }));
-  TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { PT->fft_y(F0, 0, 1, twf, -1, s); }));
+  TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { PT->fft_y(F0, 0, 1, twf, -1, c->tune.tile_y, s); }));
   transforms++;
   if (c->p.interlaced) {
     TRY(run(c, PSPEC_K_FFT_X, acc(2 * Sc), [&] { PT->fft_x(F0, F0, twf, -1, s); }));
     TRY(run(c, PSPEC_K_FFT_Z, acc(Sr + Sc), [&] { PT->r2c_z(m2, W, twh, twr, s); }));
-    TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { PT->fft_y(W, 0, 1, twf, -1, s); }));
+    TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { PT->fft_y(W, 0, 1, twf, -1, c->tune.tile_y, s); }));
     transforms++;
     TRY(run(c, PSPEC_K_COMBINE, acc(3 * Sc), [&] {
-      PT->combine_x(W, F0, twf, 1, c->p.compensate, pl.roundtrip, phase, invw, ba, pl.ctas_comb, s);
+      PT->combine_x(W, F0, twf, 1, c->p.compensate, pl.roundtrip, phase, invw, ba, ctas_comb, s);
     }));
   } else {
     TRY(run(c, PSPEC_K_COMBINE, acc(2 * Sc), [&] {
-      PT->combine_x(F0, F0, twf, 0, c->p.compensate, pl.roundtrip, phase, invw, ba, pl.ctas_comb, s);
+      PT->combine_x(F0, F0, twf, 0, c->p.compensate, pl.roundtrip, phase, invw, ba, ctas_comb, s);
     }));
   }
   if (pl.roundtrip) {
     TRY(run(c, PSPEC_K_FFT_X, acc(2 * Sc), [&] { PT->fft_x(F0, W, twf, +1, s); }));
-    TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { PT->fft_y(W, 0, 1, twf, +1, s); }));
+    TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { PT->fft_y(W, 0, 1, twf, +1, c->tune.tile_y, s); }));
     const T scale = T(2.0 / ((double)N * N * N));
     TRY(run(c, PSPEC_K_C2R_Z, acc(Sc + Sr), [&] { PT->c2r_z(W, f, twh, twr, scale, s); }));
     transforms++;
@@ -512,7 +518,7 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
       const int M = std::min(pl.group_max, nh - h0);
       // z pass with the Y_lm weights: one block holds Ms harmonics x rows rows, tz threads each
       const int tz = PT->tz;
-      const int ms_max = std::max(1, kYlmMaxThreads / tz);
+      const int ms_max = std::max(1, std::min(c->tune.ylm_harmonics, kYlmMaxThreads / tz));
       for (int hs = 0; hs < M; hs += ms_max) {
         const int Ms = std::min(ms_max, M - hs);
         int rows = std::max(1, pow2_floor(std::max(1, kYlmMaxThreads / (Ms * tz))));
@@ -521,9 +527,9 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
           PT->ylm_z(f, G + hs * stride, stride, ell, h0 + hs, Ms, twh, twr, axis, rows, s);
         }));
       }
-      TRY(run(c, PSPEC_K_FFT_Y, acc(2 * M * Sc), [&] { PT->fft_y(G, stride, M, twf, -1, s); }));
+      TRY(run(c, PSPEC_K_FFT_Y, acc(2 * M * Sc), [&] { PT->fft_y(G, stride, M, twf, -1, c->tune.tile_y, s); }));
       TRY(run(c, PSPEC_K_BIN_X, acc(Sc + M * Sc), [&] {
-        PT->bin_x(G, stride, ell, h0, M, F0, twf, SLOT_ELL0 + i, ba, pl.ctas_bin, s);
+        PT->bin_x(G, stride, ell, h0, M, F0, twf, SLOT_ELL0 + i, ba, ctas_bin, s);
       }));
       transforms += M;
     }
@@ -592,7 +598,7 @@ pspec_status do_set_randoms(Ctx* c, const pspec_catalog* r) {
   TRY(run(c, PSPEC_K_SUMS, 0.0, [&] { launch_randoms_sums(part, pl.nblk_sum, c->at<double>(pl.o_rsums), c->stream); }));
   T* r1 = c->at<T>(pl.o_rmesh1);
   T* r2 = c->p.interlaced ? c->at<T>(pl.o_rmesh2) : nullptr;
-  const bool binned = pl.max_particles >= r->count;
+  const bool binned = c->tune.paint_binned && pl.max_particles >= r->count;
   TRY(paint_one<T>(c, ar, 2, binned, r->count, r1, r2));
   return PSPEC_OK;
 }
@@ -832,7 +838,7 @@ pspec_status pspec_run_batch(void* ctx, const pspec_catalog* mocks, int32_t n_mo
                       c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->at<int>(pl.o_cur), 0, sizeof(int), c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "batch table upload");
-  const bool binned = pl.max_particles >= max_count && c->p.precision == PSPEC_FP32;
+  const bool binned = c->tune.paint_binned && pl.max_particles >= max_count && c->p.precision == PSPEC_FP32;
   const bool f64 = c->p.precision == PSPEC_FP64;
   auto one = [&]() {
     return f64 ? enqueue_mock<double>(c, binned, max_count, ells, n_ells, n_kbins, P_all, sums_all)
@@ -951,6 +957,79 @@ pspec_status pspec_wedges(const double* P, const int32_t* ells, int32_t n_ells, 
   }
   launch_wedges(P, n_ells, n_kbins, n_mu, t, out, static_cast<cudaStream_t>(stream));
   return cudaGetLastError() == cudaSuccess ? PSPEC_OK : PSPEC_ECUDA;
+}
+
+pspec_status pspec_get_tuning(void* ctx, pspec_tuning* t) {
+  if (!ctx || !t) return PSPEC_EINVAL;
+  *t = static_cast<Ctx*>(ctx)->tune;
+  return PSPEC_OK;
+}
+
+pspec_status pspec_set_tuning(void* ctx, const pspec_tuning* t) {
+  if (!ctx || !t) return PSPEC_EINVAL;
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (t->paint_binned < 0 || t->paint_binned > 1 || t->ylm_harmonics < 1 || t->ylm_harmonics > 512 ||
+      t->bin_blocks_per_sm < 0 || t->bin_blocks_per_sm > 16 || t->tile_y < 0 || t->tile_y > 1) {
+    c->err = "tuning value out of range";
+    return PSPEC_EINVAL;
+  }
+  c->tune = *t;
+  return PSPEC_OK;
+}
+
+pspec_status pspec_autotune(void* ctx, const pspec_catalog* data, const pspec_catalog* randoms, const int32_t* ells,
+                            int32_t n_ells, const double* k_edges, int32_t n_kbins, int32_t reps, pspec_tuning* best) {
+  if (!ctx || !best) return PSPEC_EINVAL;
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (reps < 1) reps = 1;
+  double* out = c->at<double>(c->pl.o_out);
+  const int nk = n_kbins;
+  cudaEvent_t e0 = take_event(c), e1 = take_event(c);
+  const bool prof = c->prof;
+  c->prof = false;
+  // time one configuration: paint + multipoles, `reps` times after one warm-up
+  auto measure = [&](const pspec_tuning& t, float* ms) -> pspec_status {
+    c->tune = t;
+    for (int r = -1; r < reps; r++) {
+      if (r == 0) cudaEventRecord(e0, c->stream);
+      TRY(pspec_paint(ctx, data, randoms, nullptr));
+      TRY(pspec_multipoles_device(ctx, ells, n_ells, k_edges, nk, out + 2 * (size_t)nk, out, out + nk));
+    }
+    cudaEventRecord(e1, c->stream);
+    cudaError_t er = cudaEventSynchronize(e1);
+    if (er != cudaSuccess) return cuda_fail(c, er, "autotune");
+    cudaEventElapsedTime(ms, e0, e1);
+    return PSPEC_OK;
+  };
+  pspec_tuning cur = c->tune;
+  float best_ms = 0.f;
+  pspec_status st = measure(cur, &best_ms);
+  // coordinate search over the knobs
+  const int tz = pass_table<float>(c->p.nmesh)->tz;
+  const int hmax = std::max(1, 512 / tz);
+  std::vector<std::vector<int>> cand = {
+      {1, 0}, {hmax, std::max(1, hmax / 2), std::max(1, hmax / 4)}, {0, 1, 2}, {0, 1}};
+  for (int knob = 0; knob < 4 && st == PSPEC_OK; knob++) {
+    for (int v : cand[knob]) {
+      pspec_tuning t = cur;
+      int* f = knob == 0 ? &t.paint_binned : knob == 1 ? &t.ylm_harmonics : knob == 2 ? &t.bin_blocks_per_sm : &t.tile_y;
+      if (*f == v) continue;
+      *f = v;
+      float ms = 0.f;
+      st = measure(t, &ms);
+      if (st != PSPEC_OK) break;
+      if (ms < best_ms) {
+        best_ms = ms;
+        cur = t;
+      }
+    }
+  }
+  c->tune = cur;
+  c->prof = prof;
+  c->pool.push_back(e0);
+  c->pool.push_back(e1);
+  *best = cur;
+  return st;
 }
 
 pspec_status pspec_get_plan_info(void* ctx, pspec_plan_info* info) {

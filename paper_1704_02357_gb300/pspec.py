@@ -46,6 +46,11 @@ class Stats(C.Structure):
                 ("W_r", C.c_double), ("n_nonfinite", C.c_int64), ("n_wrapped", C.c_int64)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("paint_binned", C.c_int32), ("ylm_harmonics", C.c_int32), ("bin_blocks_per_sm", C.c_int32),
+                ("tile_y", C.c_int32)]
+
+
 class PlanInfo(C.Structure):
     _fields_ = [("nmesh", C.c_int32), ("precision", C.c_int32), ("ell_max", C.c_int32),
                 ("tile_y", C.c_int32), ("tile_x", C.c_int32), ("tile_bin", C.c_int32), ("rows_z", C.c_int32),
@@ -83,6 +88,10 @@ SIGNATURES = [
     ("pspec_run_batch", C.c_int32, [C.c_void_p, C.POINTER(Catalog), C.c_int32, C.POINTER(C.c_int32), C.c_int32,
                                     C.POINTER(C.c_double), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.c_int32]),
+    ("pspec_get_tuning", C.c_int32, [C.c_void_p, C.POINTER(Tuning)]),
+    ("pspec_set_tuning", C.c_int32, [C.c_void_p, C.POINTER(Tuning)]),
+    ("pspec_autotune", C.c_int32, [C.c_void_p, C.POINTER(Catalog), C.POINTER(Catalog), C.POINTER(C.c_int32),
+                                   C.c_int32, C.POINTER(C.c_double), C.c_int32, C.c_int32, C.POINTER(Tuning)]),
     ("pspec_catalog_sums_noalloc", C.c_int32, [C.POINTER(Params), C.POINTER(Catalog), C.POINTER(Catalog), C.c_int32,
                                                C.c_void_p, C.c_void_p]),
 ]
@@ -245,6 +254,34 @@ class Estimator:
                                       C.c_void_p(nm.data_ptr()), int(bool(use_graph))), self._ctx)
         self._bkeep = keep
         return {"P": P, "sums": sums, "k_mean": km, "n_modes": nm, "ells": ells}
+
+    # ------------------------------------------------------------------ tuning
+    def tuning(self) -> dict:
+        t = Tuning()
+        _check(load().pspec_get_tuning(self._ctx, C.byref(t)), self._ctx)
+        return {f: getattr(t, f) for f, _ in Tuning._fields_}
+
+    def set_tuning(self, **kw):
+        cur = self.tuning()
+        cur.update({k: int(v) for k, v in kw.items()})
+        t = Tuning(*[cur[f] for f, _ in Tuning._fields_])
+        _check(load().pspec_set_tuning(self._ctx, C.byref(t)), self._ctx)
+
+    def autotune(self, data_pos, randoms_pos, ells, k_edges, reps=2, data_weight=None, data_nbar=None,
+                 randoms_weight=None, randoms_nbar=None) -> dict:
+        """Time candidate knob settings on these catalogs (native search) and keep the best."""
+        keep = []
+        d = _catalog(data_pos, data_weight, data_nbar, self.device, keep)
+        r = _catalog(randoms_pos, randoms_weight, randoms_nbar, self.device, keep)
+        ells = [int(e) for e in ells]
+        edges = np.ascontiguousarray(k_edges, dtype=np.float64)
+        el = (C.c_int32 * len(ells))(*ells)
+        best = Tuning()
+        _check(load().pspec_autotune(self._ctx, C.byref(d), C.byref(r), el, len(ells),
+                                     edges.ctypes.data_as(C.POINTER(C.c_double)), len(edges) - 1, int(reps),
+                                     C.byref(best)), self._ctx)
+        self._keep = keep
+        return {f: getattr(best, f) for f, _ in Tuning._fields_}
 
     def plan_info(self) -> dict:
         info = PlanInfo()

@@ -1,0 +1,52 @@
+"""Autotune cache: the knob settings pspec_autotune picked, per GPU and plan shape, in JSON.
+
+Key: GPU name, mesh side, precision, l_max, window, interlacing. The search itself runs in
+libpspec (pspec_autotune); this module only stores and reapplies its answer.
+"""
+from __future__ import annotations
+
+import json
+import os
+from typing import Optional
+
+DEFAULT_PATH = os.environ.get("PSPEC_TUNING_CACHE",
+                              os.path.join(os.path.expanduser("~"), ".cache", "pspec_gb300", "tuning.json"))
+
+
+def key_for(est) -> str:
+    import torch
+    p = est.params
+    name = torch.cuda.get_device_name(est.device).replace(" ", "_")
+    prec = "fp64" if p.precision else "fp32"
+    return f"{name}|N{p.nmesh}|{prec}|l{p.ell_max}|w{p.window}|i{p.interlaced}"
+
+
+def load_cache(path: str = DEFAULT_PATH) -> dict:
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def save_cache(cache: dict, path: str = DEFAULT_PATH) -> None:
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def tuned(est, data_pos, randoms_pos, ells, k_edges, path: Optional[str] = DEFAULT_PATH, reps: int = 2,
+          **cat) -> dict:
+    """Apply the cached tuning for this estimator's key, or run the autotuner and cache it."""
+    key = key_for(est)
+    cache = load_cache(path) if path else {}
+    if key in cache:
+        est.set_tuning(**cache[key])
+        return dict(cache[key], cached=True)
+    best = est.autotune(data_pos, randoms_pos, ells, k_edges, reps=reps, **cat)
+    if path:
+        cache[key] = best
+        save_cache(cache, path)
+    return dict(best, cached=False)

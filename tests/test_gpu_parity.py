@@ -263,3 +263,36 @@ def test_tile_binned_paint_falls_back_when_catalog_exceeds_capacity():
     o = E.multipoles(d, r, p, [0, 2], edges)
     g = run_gpu(p, d, r, [0, 2], edges, precision="fp32", max_particles=1000)
     check_fp32(g, o, [0, 2], scale=np.abs(o["P"][0]) + o["S"] / o["I"])
+
+
+@pytest.mark.parametrize("knobs", [dict(tile_y=1), dict(ylm_harmonics=2), dict(bin_blocks_per_sm=1),
+                                   dict(paint_binned=0), dict(tile_y=1, ylm_harmonics=3, bin_blocks_per_sm=2)])
+def test_tuning_knobs_keep_parity(knobs):
+    """Every runtime knob setting is a different launch shape of the same computation."""
+    d, r, p, edges = _offnode(64, "tsc", True, seed=21)
+    ells = [0, 2, 4, 6]
+    o = E.multipoles(d, r, p, ells, edges)
+    est = gpu_estimator(p, precision="fp32", ell_max=6, max_particles=d.size + r.size)
+    est.set_tuning(**knobs)
+    est.paint(d.pos, r.pos)
+    g = est.multipoles(ells, edges)
+    est.close()
+    check_fp32(g, o, ells, scale=np.abs(o["P"][0]) + o["S"] / o["I"])
+
+
+def test_autotune_picks_valid_knobs_and_caches(tmp_path):
+    from paper_1704_02357_gb300 import tune
+    d, r, p, edges = _offnode(64, "cic", True, seed=22)
+    ells = [0, 2, 4]
+    est = gpu_estimator(p, precision="fp32", ell_max=4, max_particles=d.size + r.size)
+    path = str(tmp_path / "tuning.json")
+    first = tune.tuned(est, d.pos, r.pos, ells, edges, path=path)
+    assert not first["cached"] and first["paint_binned"] in (0, 1) and first["tile_y"] in (0, 1)
+    second = tune.tuned(est, d.pos, r.pos, ells, edges, path=path)
+    assert second["cached"] and all(second[k] == first[k] for k in ("paint_binned", "ylm_harmonics",
+                                                                      "bin_blocks_per_sm", "tile_y"))
+    est.paint(d.pos, r.pos)
+    g = est.multipoles(ells, edges)
+    est.close()
+    o = E.multipoles(d, r, p, ells, edges)
+    check_fp32(g, o, ells, scale=np.abs(o["P"][0]) + o["S"] / o["I"])
