@@ -55,10 +55,21 @@ def k_edges(nmesh=NMESH, box=BOX, dk=0.005):
     return dk * np.arange(n + 1)
 
 
+_FIELDS = {}
+
+
+def field_for(geo, seed_offset=0):
+    """The lognormal field of the survey workload (generated once per process)."""
+    import synth
+    if seed_offset not in _FIELDS:
+        _FIELDS[seed_offset] = synth.lognormal_field(256, geo.box_size, geo.box_corner, seed=3 + 1000 * seed_offset)
+    return _FIELDS[seed_offset]
+
+
 def workload(seed_offset=0):
     import synth
     geo = synth.survey_geometry(box_size=BOX)
-    fld = synth.lognormal_field(256, geo.box_size, geo.box_corner, seed=3 + 1000 * seed_offset)
+    fld = field_for(geo, seed_offset)
     data = synth.survey_catalog(fld, geo, nbar=NBAR, seed=33 + 1000 * seed_offset)
     randoms = synth.survey_randoms(20 * data.size, geo, seed=4 + 1000 * seed_offset)
     return geo, data, randoms
@@ -269,6 +280,123 @@ def run_reference(args):
     return 0
 
 
+# --------------------------------------------------------------------------- side measurements
+def _timed_events(fn, stream, reps):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def batched_measurement(est_for_unused, data, randoms, edges, dev, stream, n_mocks=8):
+    """512^3, l <= 4, FP32: mocks (90% subsamples of the survey catalog, seeded) against the
+    cached randoms meshes, one graph replay per mock."""
+    import torch
+    from paper_1704_02357_gb300 import Estimator
+    rng = np.random.default_rng(11)
+    mocks = [torch.as_tensor(data.pos[rng.random(data.size) < 0.9], device=dev) for _ in range(n_mocks)]
+    est = Estimator(nmesh=NMESH, box_size=BOX, box_corner=_corner(), window="cic", interlaced=True, compensate=True,
+                    precision="fp32", ell_max=4, P0=P0, nbar=NBAR, max_kbins=len(edges) - 1,
+                    max_particles=max(int(m.shape[0]) for m in mocks), cache_randoms=True, device=dev, stream=stream)
+    est.set_randoms(torch.as_tensor(randoms.pos, device=dev))
+    est.run_batch(mocks[:2], ELLS, edges)  # capture + warm-up
+    l0 = est.plan_info()["kernel_launches"]
+    ms = _timed_events(lambda: est.run_batch(mocks, ELLS, edges), stream, 1)
+    launches = est.plan_info()["kernel_launches"] - l0
+    est.close()
+    return {"value": n_mocks / (ms / 1e3), "unit": "sets/s", "ms_per_set": ms / n_mocks, "mocks": n_mocks,
+            "randoms": "painted once, cached", "graph": True, "gpu_launches": launches}
+
+
+def campaign_measurement(geo, dev, stream, rank, n_mocks=16):
+    """Mock campaign: N_d log-uniform in [3e5, 3e6] (seeds 100..), meshes 256^3 / 384^3 by
+    seed parity, l <= 4, CIC + interlacing, FP32, one shared randoms catalog of 20x the largest
+    mock painted once per mesh side; unit weights (P0 = 0) so that one randoms mesh serves
+    mocks of every density. Mocks are random subsets of one dense lognormal catalog."""
+    import synth
+    import torch
+    from paper_1704_02357_gb300.batch import BatchRunner
+    spec = synth.mock_batch_spec(n_mocks=n_mocks)
+    fld = field_for(geo, rank)
+    dense = synth.survey_catalog(fld, geo, nbar=1.2e-3, seed=77 + 1000 * rank)
+    nmax = max(n for _, n, _ in spec)
+    randoms = synth.survey_randoms(20 * nmax, geo, seed=78 + 1000 * rank)
+    mocks, meshes = [], []
+    for s_, nd, nm in spec:
+        rng = np.random.default_rng(s_)
+        idx = rng.choice(dense.size, size=min(nd, dense.size), replace=False)
+        mocks.append(torch.as_tensor(dense.pos[idx], device=dev))
+        meshes.append(nm)
+    rdev = torch.as_tensor(randoms.pos, device=dev)
+    br = BatchRunner(BOX, _corner(), rdev, window="cic", interlaced=True, precision="fp32", ell_max=4, P0=0.0,
+                     nbar=0.0, device=dev, stream=stream)
+    ef = lambda n: k_edges(n)
+    br.run(mocks[:4], meshes[:4], ELLS, ef)  # contexts, randoms meshes, graphs
+    torch.cuda.synchronize()
+    ms = _timed_events(lambda: br.run(mocks, meshes, ELLS, ef), stream, 1)
+    br.close()
+    return {"value": n_mocks / (ms / 1e3), "unit": "sets/s", "mocks": n_mocks, "meshes": "256^3/384^3 alternating",
+            "n_data": [int(m.shape[0]) for m in mocks], "randoms": int(randoms.size), "graph": True}
+
+
+def serving_measurement(geo, dev, rank, n_requests=20, load=0.5):
+    """Served stream: Poisson arrivals (seed 5) of catalogs with 1e5-5e6 particles
+    (log-uniform), meshes from {128, 256, 512, 768, 1024}^3 and l_max in {4, 16} uniformly,
+    FP32, admitted by workspace footprint against a 120 GB budget; mean inter-arrival set to
+    `load` of the measured mean service time."""
+    import synth
+    import torch
+    from paper_1704_02357_gb300.serve import Server, Request, latency_summary
+    rng = np.random.default_rng(5)
+    fld = field_for(geo, rank)
+    dense = synth.survey_catalog(fld, geo, nbar=1.9e-3, seed=99 + 1000 * rank)
+    randoms = synth.survey_randoms(2 * 10 ** 7, geo, seed=98 + 1000 * rank)
+    rdev = torch.as_tensor(randoms.pos, device=dev)
+    meshes = [128, 256, 512, 768, 1024]
+    reqs = []
+    for i in range(n_requests):
+        n = int(round(math.exp(rng.uniform(math.log(1e5), math.log(5e6)))))
+        idx = rng.choice(dense.size, size=min(n, dense.size), replace=False)
+        nm = int(rng.choice(meshes))
+        lm = int(rng.choice([4, 16]))
+        reqs.append(Request(rid=i, nmesh=nm, ell_max=lm, pos=torch.as_tensor(dense.pos[idx], device=dev),
+                            k_edges=k_edges(nm)))
+    gb = 1 << 30
+    mgb = lambda n, l: (8 * (n ** 3) * 4 if n >= 768 else 0)  # at most 8 spectra per group at 768^3+
+    srv = Server(BOX, _corner(), randoms_for=lambda n: rdev, hbm_budget=120 * gb, window="cic", interlaced=True,
+                 P0=P0, nbar=NBAR, max_kbins=512, max_particles=5 * 10 ** 6 + 1, max_group_bytes_for=mgb,
+                 max_slots_per_shape=1, device=dev)
+    # service time of each shape alone (warms contexts and graphs): sets the arrival rate
+    svc = []
+    for key in sorted({(r.nmesh, r.ell_max) for r in reqs}):
+        r0 = next(r for r in reqs if (r.nmesh, r.ell_max) == key)
+        probe = Request(rid=-1, nmesh=key[0], ell_max=key[1], pos=r0.pos, k_edges=r0.k_edges)
+        for _ in range(2):
+            t = time.perf_counter()
+            srv.submit(probe)
+            while srv.busy():
+                srv.step()
+            dt = time.perf_counter() - t
+        svc.append(dt)
+    mean_service = float(np.mean(svc))
+    srv.done.clear()
+    gaps = rng.exponential(mean_service / load, size=n_requests)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    t0 = time.perf_counter()
+    done = srv.run(reqs, arrivals)
+    wall = time.perf_counter() - t0
+    out = latency_summary(done, wall)
+    out.update({"load": load, "mean_service_ms_alone": mean_service * 1e3, "hbm_budget_gb": 120,
+                "contexts": len(srv.slots)})
+    srv.close()
+    return out
+
+
 # --------------------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -354,8 +482,10 @@ def main():
             ms = float(t.item())
         return ms, launches, kt, P
 
-    # ---- headline: FP32, l = 0, 2, 4
+    # ---- headline: FP32, l = 0, 2, 4 (knobs from the autotuner, cached per GPU and plan shape)
     est = est_for("fp32", max(ells_main))
+    from paper_1704_02357_gb300 import tune
+    tuning = tune.tuned(est, dpos, rpos, ells_main, edges)
     uuid = None
     try:
         uuid = str(torch.cuda.get_device_properties(dev).uuid)
@@ -422,6 +552,15 @@ def main():
                                         "ms_per_set": ms64 / max(3, args.steps // 4)}
         e64.close()
 
+    if not args.quick and nmesh == NMESH:
+        side["fp32_batched_ell_max_4"] = batched_measurement(est_for, data, randoms, edges, dev, stream)
+        est.close()
+        torch.cuda.empty_cache()
+        side["mock_campaign"] = campaign_measurement(geo, dev, stream, rank)
+        torch.cuda.empty_cache()
+        side["serving"] = serving_measurement(geo, dev, rank)
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and nmesh == NMESH:
         del dh, rh
@@ -451,10 +590,12 @@ def main():
             "plan": {k: info[k] for k in ("tile_y", "tile_x", "tile_bin", "rows_z", "group_max", "bin_ctas",
                                           "sh_transforms", "transforms_executed")},
             "cpu_baseline": cpu,
+            "tuning": tuning,
         }
         line.update(side)
         print(json.dumps(line), flush=True)
-    est.close()
+    if est._ctx:
+        est.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0

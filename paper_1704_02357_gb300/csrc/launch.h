@@ -104,7 +104,8 @@ constexpr int elems_per_thread(int N) { return N % 3 == 0 ? 24 : 8; }
 constexpr int col_tile(int N) {
   const int tc = N / elems_per_thread(N);
   int cap = 512 / tc < 16 ? 512 / tc : 16, tw = 1;
-  while (tw * 2 <= cap && (N / 2) % (tw * 2) == 0) tw *= 2;
+  // N * TW <= 4096 keeps two FP64 tiles (binning pass) plus the bins within shared memory
+  while (tw * 2 <= cap && (N / 2) % (tw * 2) == 0 && N * tw * 2 <= 4096) tw *= 2;
   return tw;
 }
 constexpr int z_rows(int N) {

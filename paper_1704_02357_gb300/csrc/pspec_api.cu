@@ -15,6 +15,7 @@ namespace {
 
 constexpr size_t kAlign = 256;
 constexpr size_t kSmemBudget = 200 * 1024;   // one block
+constexpr size_t kSmemMaxBlock = 227 * 1024; // per-block limit of the device
 constexpr int kMaxElls = PSPEC_MAX_ELL / 2 + 1;
 constexpr int kYlmMaxThreads = 512;
 
@@ -99,6 +100,11 @@ pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl,
   int m_mem = p->max_group_bytes > 0 ? (int)(p->max_group_bytes / (int64_t)pl->Sc) : nharm;
   pl->group_max = p->ell_max == 0 ? 0 : std::max(1, std::min(nharm, m_mem));
 
+  {
+    const size_t need = f64 ? std::max(pl->td->smem_bin(max_kbins), pl->td->smem_combine(max_kbins))
+                            : std::max(pl->tf->smem_bin(max_kbins), pl->tf->smem_combine(max_kbins));
+    if (need > kSmemMaxBlock) { *why = "max_kbins too large for this mesh (shared memory)"; return PSPEC_EINVAL; }
+  }
   if (f64) {
     pl->ctas_comb = pl->td->ctas(0, max_kbins, nsm);
     pl->ctas_bin = pl->td->ctas(1, max_kbins, nsm);
