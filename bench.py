@@ -147,8 +147,10 @@ def hbm_peak():
         return 6800.0, "fallback"
 
 
-def traffic_for(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if it still matches the source."""
+def traffic_for(kernel, alg_bytes_per_launch):
+    """DRAM bytes per launch: the DRAM/algorithmic byte ratio of one ncu capture of this kernel
+    (a smaller case; traffic grows with the spectra a launch processes) times this run's
+    algorithmic bytes per launch. None when no capture matches the current kernel source."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         t = json.load(open(p))
@@ -157,7 +159,7 @@ def traffic_for(kernel):
     ent = t.get("kernels", {}).get(kernel)
     if not ent or ent.get("source_hash") != source_hash():
         return None
-    return ent.get("dram_bytes_per_launch")
+    return ent["dram_bytes_per_algorithmic_byte"] * alg_bytes_per_launch
 
 
 def source_hash():
@@ -578,7 +580,7 @@ def main():
                        "parallelism": f"{ws} GPU(s), one independent catalog per GPU"},
             "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_kind,
-                         "traffic": traffic_for(dname),
+                         "traffic": traffic_for(dname, d["bytes"] / max(1, d["launches"])),
                          "algorithmic_bytes_per_launch": d["bytes"] / max(1, d["launches"])},
             "step_roofline": {"model_bytes_per_set": total_bytes,
                               "achieved_GBps": total_bytes / 1e9 / (ms_step / 1e3),
