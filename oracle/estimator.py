@@ -141,7 +141,7 @@ def paint(pos: np.ndarray, values: np.ndarray, params: Params, shift: float = 0.
     n = params.nmesh
     u = (np.asarray(pos, dtype=np.float64) - np.asarray(params.box_corner, dtype=np.float64)) \
         / params.cell - shift
-    mesh = np.zeros((n, n, n))
+    mesh = np.zeros(n * n * n)
     bx, wx = window_weights_1d(u[:, 0], params.window)
     by, wy = window_weights_1d(u[:, 1], params.window)
     bz, wz = window_weights_1d(u[:, 2], params.window)
@@ -151,8 +151,8 @@ def paint(pos: np.ndarray, values: np.ndarray, params: Params, shift: float = 0.
             ib = (by + b) % n
             for c, wcz in enumerate(wz):
                 ic = (bz + c) % n
-                np.add.at(mesh, (ia, ib, ic), values * wa * wb * wcz)
-    return mesh
+                mesh += np.bincount((ia * n + ib) * n + ic, weights=values * wa * wb * wcz, minlength=n ** 3)
+    return mesh.reshape(n, n, n)
 
 
 # --------------------------------------------------------------------------- k-space helpers

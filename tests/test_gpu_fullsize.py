@@ -1,0 +1,44 @@
+"""Full-size parity: the survey workload of the benchmark (512^3, CIC + interlacing,
+l = 0, 2, 4, FP32) against the FP64 oracle, bin by bin, under the stated tolerances.
+
+Higher multipoles (l <= 16) are checked against the oracle at 96^3 in test_gpu_parity.py;
+at 512^3 the oracle would need ~150 full transforms and Y_lm evaluations (tens of minutes).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import estimator as E
+from tests._parity import check_fp32, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1704_02357_gb300 import build
+    build.build()
+
+
+def test_survey_512_l4_matches_oracle():
+    geo = synth.survey_geometry(box_size=2000.0)
+    fld = synth.lognormal_field(256, geo.box_size, geo.box_corner, seed=3)
+    d = synth.survey_catalog(fld, geo, nbar=3e-4, seed=33)
+    r = synth.survey_randoms(20 * d.size, geo, seed=4)
+    d.nbar = None
+    p = E.Params(nmesh=512, box_size=2000.0, box_corner=tuple(geo.box_corner), window="cic", interlaced=True,
+                 compensate=True, P0=1e4, nbar=3e-4)
+    kn = math.pi * 512 / 2000.0
+    edges = 0.005 * np.arange(int(kn / 0.005) + 1)
+    ells = [0, 2, 4]
+    g = run_gpu(p, d, r, ells, edges, precision="fp32", max_particles=d.size + r.size)
+    o = E.multipoles(d, r, p, ells, edges)
+    np.testing.assert_array_equal(g["n_modes"], o["n_modes"])
+    np.testing.assert_allclose(g["k_mean"], o["k_mean"], rtol=1e-6)
+    assert abs(g["stats"]["alpha"] - o["alpha"]) <= 1e-14 * o["alpha"]
+    rep = {}
+    check_fp32(g, o, ells, report=rep)
+    assert rep[0]["bins_checked"] == len(edges) - 1 and rep[2]["bins_checked"] > 20 and rep[4]["bins_checked"] > 0
+    print("full-size parity:", rep)
