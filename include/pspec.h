@@ -83,8 +83,15 @@ typedef struct {
   int64_t max_particles;   /* data + randoms the tile-binned paint is sized for (FP32 meshes);
                               0, a larger catalog pair or FP64 meshes use direct atomic painting */
   int32_t cache_randoms;   /* 0/1: reserve meshes for pspec_set_randoms / pspec_run_batch */
-  int32_t reserved;        /* 0 */
+  int32_t ylm_table;       /* FP32 contexts, l_max >= 2: 0 = hold Y_lm(khat) of every stored mode
+                              for l = 2..l_max, evaluated in FP64 at creation and rounded once
+                              to FP32 (4 bytes per mode and harmonic: 41 GB at 512^3, l_max = 16),
+                              when that takes at most PSPEC_YLM_TABLE_AUTO_MAX bytes; -1 = never.
+                              Without the table the binning pass evaluates Y_lm(khat) in FP32;
+                              its rounding is biased by a few percent of an ulp over a k shell,
+                              which lets ~4e-9 of the shot-noise power into P_l (l >= 2) */
 } pspec_params;
+#define PSPEC_YLM_TABLE_AUTO_MAX ((int64_t)64 << 30)
 
 typedef struct {
   const void* pos;         /* device, count x 3 row-major, dtype per pos_dtype */
@@ -141,6 +148,22 @@ pspec_status pspec_multipoles_device(void* ctx, const int32_t* ells, int32_t n_e
  * Enqueued on `stream` without synchronising. */
 pspec_status pspec_wedges(const double* P, const int32_t* ells, int32_t n_ells, int32_t n_kbins,
                           const double* mu_edges, int32_t n_mu, double* out, void* stream);
+
+/* Splitting one catalog's multipoles across GPUs (the 2l+1 transforms of a multipole are
+ * independent, Sec. 2.1). The harmonics of the requested multipoles l >= 2, listed l by l
+ * (order of `ells`) and within l as m = 0, +1, -1, +2, -2, ..., form one list of
+ * sum(2l+1) items. pspec_multipoles_range computes, on the painted meshes, the raw FP64 bin
+ * sums of items [q0, q1) into the DEVICE array bins (1 + n_ells) x n_kbins: slot 0 holds
+ * sum mult |F0|^2 when include_p0 (else zeros), slot 1 + i the sum for ells[i] (zeros for
+ * l = 0 and for multipoles outside the range). Adding up the arrays of calls that cover the
+ * list once (say one per GPU, then an all-reduce) and passing the sum to pspec_finalize_bins
+ * (same context state, same ells and k_edges) gives what pspec_multipoles_device gives.
+ * Both enqueue on the context's stream without synchronising. */
+pspec_status pspec_multipoles_range(void* ctx, const int32_t* ells, int32_t n_ells, const double* k_edges,
+                                    int32_t n_kbins, int32_t q0, int32_t q1, int32_t include_p0, double* bins);
+pspec_status pspec_finalize_bins(void* ctx, const double* bins, const int32_t* ells, int32_t n_ells,
+                                 const double* k_edges, int32_t n_kbins, double* P_dev, double* k_mean_dev,
+                                 double* n_modes_dev);
 
 /* Batched mocks sharing one randoms catalog (the batching pattern of the mock campaigns
  * that motivate the method, Sec. 1 and Sec. 5). Needs a context created with cache_randoms = 1.
@@ -211,6 +234,7 @@ typedef struct {
   int64_t transforms_executed;                /* 3-D transforms of the last multipoles call */
   int64_t kernel_launches;                    /* cumulative kernels launched by this context */
   double model_bytes_last;                    /* algorithmic HBM bytes of the last paint+multipoles */
+  int64_t ylm_table_bytes;                    /* Y_lm(khat) table held (0: evaluated per mode) */
 } pspec_plan_info;
 pspec_status pspec_get_plan_info(void* ctx, pspec_plan_info* info);
 

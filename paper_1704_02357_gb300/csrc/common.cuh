@@ -1,5 +1,6 @@
 // Device-side building blocks shared by the libpspec kernels: complex arithmetic,
-// the shared-memory Stockham FFT stage, and the real spherical-harmonic recurrence.
+// unit-modulus table factors, the small in-register DFTs, and the real spherical-harmonic
+// recurrence.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -26,17 +27,53 @@ template <typename C> __device__ __forceinline__ C cmul_i(C a, int sgn) {
   return sgn > 0 ? mk(-a.y, a.x) : mk(a.y, -a.x);
 }
 
-// ------------------------------------------------------------------ FFT plan
-// A length-L transform as a product of radices (2, 3, 4, 8), applied as Stockham
-// auto-sort stages. ns[s] is the product of the radices before stage s.
-constexpr int kMaxStages = 16;
-struct FftPlan {
-  int L;
-  int nst;
-  int rad[kMaxStages];
-  int ns[kMaxStages];
+// ------------------------------------------------------------------ unit-modulus factors
+// Twiddles and phase factors as the tables hold them. Rounded to FP32, (cos, sin) lies off the
+// unit circle by up to ~6e-8 with a negative mean over small tables; applied in every stage
+// of every axis that becomes a gain bias of ~1e-7 on |F|^2 that also depends on the mode's
+// index digits (the shot noise then leaks into P_0 and P_4 at high k). The FP32 entry is
+// therefore a pair hi + lo per component ({c_hi, s_hi, c_lo, s_lo}, lo = the rounding error
+// of hi) and a product folds a*lo into the roundings of the exact products a*hi. A correction
+// added after rounding would be lost: it is below half an ulp of an already rounded value.
+template <typename T> struct UnitOf;
+template <> struct UnitOf<float> { using type = float4; };   // {c_hi, s_hi, c_lo, s_lo}
+template <> struct UnitOf<double> { using type = double2; };  // {cos, sin}
+template <typename T> using ux = typename UnitOf<T>::type;
+template <typename C> struct BaseOf;
+template <> struct BaseOf<float2> { using type = float; };
+template <> struct BaseOf<double2> { using type = double; };
+template <typename C> using ux_of = ux<typename BaseOf<C>::type>;
+
+__device__ __forceinline__ float4 ldg_u(const float4* p) { return __ldg(p); }
+__device__ __forceinline__ double2 ldg_u(const double2* p) { return __ldg(p); }
+__device__ __forceinline__ float4 uconj(float4 w) { return make_float4(w.x, -w.y, w.z, -w.w); }
+__device__ __forceinline__ double2 uconj(double2 w) { return make_double2(w.x, -w.y); }
+// a * w
+__device__ __forceinline__ float2 umul(float2 a, float4 w) {
+  const float lx = fmaf(a.x, w.z, -a.y * w.w), ly = fmaf(a.x, w.w, a.y * w.z);
+  return make_float2(fmaf(a.x, w.x, fmaf(-a.y, w.y, lx)), fmaf(a.x, w.y, fmaf(a.y, w.x, ly)));
+}
+__device__ __forceinline__ double2 umul(double2 a, double2 w) {
+  return make_double2(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
+}
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+// x * K for an irrational constant K: in FP32 as x*K_hi + x*K_lo (K_lo = K - K_hi), so that
+// the product carries no systematic rounding of K (a rounded K = sqrt(1/2) alone scales a
+// quarter of every radix-8 stage's output power by 1 - 3.4e-8).
+template <typename T> struct ConstMul;
+template <> struct ConstMul<float> {
+  float hi, lo;
+  __device__ __forceinline__ constexpr ConstMul(double k) : hi((float)k), lo((float)(k - (double)(float)k)) {}
+  __device__ __forceinline__ float operator()(float x) const { return fmaf(x, hi, x * lo); }
+};
+template <> struct ConstMul<double> {
+  double k;
+  __device__ __forceinline__ constexpr ConstMul(double k_) : k(k_) {}
+  __device__ __forceinline__ double operator()(double x) const { return x * k; }
 };
 
+// ------------------------------------------------------------------ butterflies
 // Small DFTs in registers. dir = -1: exp(-2 pi i jk/R) (forward); +1: inverse.
 template <typename C, int R> struct Dft;
 
@@ -63,16 +100,16 @@ template <typename C> struct Dft<C, 4> {
 
 template <typename C> struct Dft<C, 8> {
   static __device__ __forceinline__ void run(C* v, int dir) {
-    using T = decltype(v[0].x);
-    const T h = T(0.70710678118654752440);
+    using T = typename BaseOf<C>::type;
+    const ConstMul<T> h(0.70710678118654752440);
     C e[4] = {v[0], v[2], v[4], v[6]};
     C o[4] = {v[1], v[3], v[5], v[7]};
     Dft<C, 4>::run(e, dir);
     Dft<C, 4>::run(o, dir);
     // twiddles w8^k = exp(dir * 2 pi i k / 8), k = 0..3
-    C o1 = mk(h * (o[1].x - dir * o[1].y), h * (o[1].y + dir * o[1].x));  // o1 * (1 + dir i)/sqrt2
-    C o2 = cmul_i(o[2], dir);                                               // o2 * (dir i)
-    C o3 = mk(h * (-o[3].x - dir * o[3].y), h * (-o[3].y + dir * o[3].x)); // o3 * (-1 + dir i)/sqrt2
+    C o1 = mk(h(o[1].x - dir * o[1].y), h(o[1].y + dir * o[1].x));   // o1 * (1 + dir i)/sqrt2
+    C o2 = cmul_i(o[2], dir);                                          // o2 * (dir i)
+    C o3 = mk(h(-o[3].x - dir * o[3].y), h(-o[3].y + dir * o[3].x));  // o3 * (-1 + dir i)/sqrt2
     v[0] = cadd(e[0], o[0]);
     v[4] = csub(e[0], o[0]);
     v[1] = cadd(e[1], o1);
@@ -86,80 +123,18 @@ template <typename C> struct Dft<C, 8> {
 
 template <typename C> struct Dft<C, 3> {
   static __device__ __forceinline__ void run(C* v, int dir) {
-    using T = decltype(v[0].x);
-    const T s = T(0.86602540378443864676) * T(dir);  // sin(2 pi/3) with the direction's sign
+    using T = typename BaseOf<C>::type;
+    const ConstMul<T> s3(0.86602540378443864676);  // sin(2 pi/3)
     C t = cadd(v[1], v[2]);
     C u = csub(v[1], v[2]);
     C m = mk(v[0].x - T(0.5) * t.x, v[0].y - T(0.5) * t.y);
-    C isu = mk(-s * u.y, s * u.x);  // i s u
+    const T su_x = s3(u.x) * T(dir), su_y = s3(u.y) * T(dir);
+    C isu = mk(-su_y, su_x);  // i s u, s = dir sin(2 pi/3)
     v[0] = cadd(v[0], t);
     v[1] = cadd(m, isu);
     v[2] = csub(m, isu);
   }
 };
-
-// One Stockham stage over `nseq` sequences of length L, from `in` to `out` (both shared).
-// Element e of sequence q sits at q*seq_stride + e*el_stride. Butterfly bf handles
-// inputs j + r L/R and writes outputs (j - k) R + k + r Ns, k = j mod Ns, after the
-// twiddles w_L^{r k L/(Ns R)} from `tw` (tw[t] = exp(-2 pi i t / L)).
-template <typename C, int R>
-__device__ __forceinline__ void stockham_stage(const C* in, C* out, int nseq, int L, int Ns,
-                                               int seq_stride, int el_stride, bool seq_fast,
-                                               const C* tw, int dir) {
-  const int LR = L / R;
-  const int total = nseq * LR;
-  const int tstep = L / (Ns * R);
-  for (int bf = threadIdx.x; bf < total; bf += blockDim.x) {
-    int q, j;
-    if (seq_fast) {
-      q = bf % nseq;
-      j = bf / nseq;
-    } else {
-      j = bf % LR;
-      q = bf / LR;
-    }
-    const int k = j % Ns;
-    C v[R];
-    const C* ip = in + q * seq_stride;
-#pragma unroll
-    for (int r = 0; r < R; r++) v[r] = ip[(j + r * LR) * el_stride];
-    if (Ns > 1) {
-#pragma unroll
-      for (int r = 1; r < R; r++) {
-        C w = tw[r * k * tstep];
-        if (dir > 0) w.y = -w.y;
-        v[r] = cmul(v[r], w);
-      }
-    }
-    Dft<C, R>::run(v, dir);
-    const int base = (j - k) * R + k;
-    C* op = out + q * seq_stride;
-#pragma unroll
-    for (int r = 0; r < R; r++) op[(base + r * Ns) * el_stride] = v[r];
-  }
-}
-
-// Full transform of every sequence in shared memory, ping-ponging between a and b.
-// Returns the buffer holding the result (natural order). Ends with __syncthreads().
-template <typename C>
-__device__ C* fft_smem(C* a, C* b, const FftPlan& p, int nseq, int seq_stride, int el_stride,
-                       bool seq_fast, const C* tw, int dir) {
-  C* in = a;
-  C* out = b;
-  for (int s = 0; s < p.nst; s++) {
-    switch (p.rad[s]) {
-      case 8: stockham_stage<C, 8>(in, out, nseq, p.L, p.ns[s], seq_stride, el_stride, seq_fast, tw, dir); break;
-      case 4: stockham_stage<C, 4>(in, out, nseq, p.L, p.ns[s], seq_stride, el_stride, seq_fast, tw, dir); break;
-      case 3: stockham_stage<C, 3>(in, out, nseq, p.L, p.ns[s], seq_stride, el_stride, seq_fast, tw, dir); break;
-      default: stockham_stage<C, 2>(in, out, nseq, p.L, p.ns[s], seq_stride, el_stride, seq_fast, tw, dir); break;
-    }
-    __syncthreads();
-    C* t = in;
-    in = out;
-    out = t;
-  }
-  return in;
-}
 
 // ------------------------------------------------------------------ real Y_lm recurrence
 // Reduced, normalised associated Legendre functions q_l^a(z) (the sin^a(theta) factor is
@@ -172,19 +147,42 @@ __device__ C* fft_smem(C* a, C* b, const FftPlan& p, int nseq, int seq_stride, i
 // Y_{l,-a} = sqrt2 q_l^a Im(x+iy)^a. Tables are computed in FP64 on the host.
 constexpr int kLmax = 16;
 constexpr int kLdim = kLmax + 1;
+// In FP32 the coefficients A and B are split into hi + lo (lo = the rounding error of hi)
+// and lo enters the roundings of the exact products: rounded coefficients alone would change
+// the shape of q_l^a(z) by ~1e-7, an error smooth over the sphere whose shell averages are
+// not zero, through which the k-independent shot-noise term leaks into P_l (l >= 2).
 template <typename T> struct YTab {
   T c[kLdim];
   T A[kLdim * kLdim];  // [l * kLdim + a]
   T B[kLdim * kLdim];
+  T Al[kLdim * kLdim];  // lo parts (FP32 only; zero in FP64)
+  T Bl[kLdim * kLdim];
 };
 
-template <typename T>
+// HILO = false: coefficients rounded to T only (the real-space weights Y_lm(rhat), whose
+// smooth errors only rescale the k-independent noise term and do not leak; measured).
+template <typename T, bool HILO = true>
 __device__ __forceinline__ T ylm_q(const YTab<T>& t, int ell, int a, T z) {
   T q2 = t.c[a];
   if (ell == a) return q2;
-  T q1 = t.A[(a + 1) * kLdim + a] * z * q2;
+  const int i1 = (a + 1) * kLdim + a;
+  T q1;
+  if constexpr (sizeof(T) == 4 && HILO) {
+    const T zq = z * q2;
+    q1 = fmaf(t.A[i1], zq, t.Al[i1] * zq);
+  } else {
+    q1 = t.A[i1] * z * q2;
+  }
   for (int l = a + 2; l <= ell; l++) {
-    T q = t.A[l * kLdim + a] * (z * q1 - t.B[l * kLdim + a] * q2);
+    const int i = l * kLdim + a;
+    T q;
+    if constexpr (sizeof(T) == 4 && HILO) {
+      const T u = fmaf(z, q1, -(t.Bl[i] * q2));  // z q1 - B_lo q2
+      const T s = fmaf(-t.B[i], q2, u);          // - B_hi q2 + u
+      q = fmaf(t.A[i], s, t.Al[i] * s);           // (A_hi + A_lo) s
+    } else {
+      q = t.A[i] * (z * q1 - t.B[i] * q2);
+    }
     q2 = q1;
     q1 = q;
   }
@@ -195,26 +193,21 @@ __device__ __forceinline__ T ylm_q(const YTab<T>& t, int ell, int a, T z) {
 __host__ __device__ __forceinline__ int harm_a(int h) { return (h + 1) >> 1; }
 __host__ __device__ __forceinline__ int harm_sign(int h) { return h == 0 ? 0 : ((h & 1) ? 1 : -1); }
 
+// 1/sqrt(x) to within about half an ulp. In FP32 the hardware approximation is refined by one
+// Newton step: its error is the same for every mode of a shell (same |n|^2), and as the
+// reduced q_l^a(z) are not homogeneous in the direction's length, an unrefined error would
+// change the shape of Y_lm over the shell (leaking the shot noise into P_l, l >= 2).
 template <typename T> __device__ __forceinline__ T rsqrt_t(T x);
-template <> __device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ float rsqrt_t<float>(float x) {
+  const float y = rsqrtf(x);
+  const float e = fmaf(-(x * y), y, 1.0f);  // 1 - x y^2
+  return fmaf(0.5f * y, e, y);
+}
 template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return 1.0 / sqrt(x); }
-
-// Y_{l,m(h)} at the direction of (vx, vy, vz) with squared length r2 > 0.
-template <typename T>
-__device__ __forceinline__ T ylm_dir(const YTab<T>& t, int ell, int h, T vx, T vy, T vz, T r2) {
-  const T inv = rsqrt_t<T>(r2);
-  const T x = vx * inv, y = vy * inv, z = vz * inv;
-  const int a = harm_a(h);
-  T q = ylm_q<T>(t, ell, a, z);
-  if (a == 0) return q;
-  T pr = x, pi = y;  // (x + i y)^a
-  for (int s = 1; s < a; s++) {
-    T nr = pr * x - pi * y;
-    pi = pr * y + pi * x;
-    pr = nr;
-  }
-  const T sq2 = T(1.41421356237309504880);
-  return sq2 * q * (harm_sign(h) > 0 ? pr : pi);
+// The plain hardware approximation (FP32), for the real-space directions rhat.
+template <typename T> __device__ __forceinline__ T rsqrt_fast(T x) {
+  if constexpr (sizeof(T) == 4) return rsqrtf(x);
+  else return 1.0 / sqrt(x);
 }
 
 }  // namespace pspec

@@ -90,19 +90,20 @@ __device__ __forceinline__ int sidx(int seq, int pos) {
 template <typename C> __device__ __forceinline__ C ldg_c(const C* p) { return __ldg(p); }
 
 template <typename C, int E, int L, int R, int NS, bool LAST, int LAYOUT, int NSEQ, int DIR>
-__device__ __forceinline__ void stage_ct(C (&v)[E], C* sm, int t, int seq, const C* __restrict__ tw) {
+__device__ __forceinline__ void stage_ct(C (&v)[E], C* sm, int t, int seq, const ux_of<C>* __restrict__ tw) {
+  using U = ux_of<C>;
   constexpr int Q = E / R;
   constexpr int Tc = L / E;
   constexpr int TSTEP = L / (NS * R);
   // With NS | Tc every butterfly of this thread has k = t mod NS: load its twiddles once.
   constexpr bool kShared = (Q > 1) && (NS > 1) && !LAST && (NS <= Tc);
-  C ws[kShared ? R : 1];
+  U ws[kShared ? R : 1];
   if constexpr (kShared) {
     const int k = t & (NS - 1);
 #pragma unroll
     for (int r = 1; r < R; r++) {
-      ws[r] = ldg_c(tw + r * k * TSTEP);
-      if (DIR > 0) ws[r].y = -ws[r].y;
+      ws[r] = ldg_u(tw + r * k * TSTEP);
+      if (DIR > 0) ws[r] = uconj(ws[r]);
     }
   }
 #pragma unroll
@@ -115,14 +116,14 @@ __device__ __forceinline__ void stage_ct(C (&v)[E], C* sm, int t, int seq, const
     if constexpr (NS > 1) {
 #pragma unroll
       for (int r = 1; r < R; r++) {
-        C w;
+        U w;
         if constexpr (kShared) {
           w = ws[r];
         } else {
-          w = ldg_c(tw + r * k * TSTEP);
-          if (DIR > 0) w.y = -w.y;
+          w = ldg_u(tw + r * k * TSTEP);
+          if (DIR > 0) w = uconj(w);
         }
-        u[r] = cmul(u[r], w);
+        u[r] = umul(u[r], w);
       }
     }
     Dft<C, R>::run(u, DIR);
@@ -142,7 +143,7 @@ __device__ __forceinline__ void stage_ct(C (&v)[E], C* sm, int t, int seq, const
 // buffer is free again when it returns. NSEQ is the number of interleaved sequences
 // (kInterleaved only).
 template <typename C, int E, int L, int LAYOUT, int NSEQ, int DIR>
-__device__ __forceinline__ void fft_ct(C (&v)[E], C* sm, int t, int seq, const C* __restrict__ tw) {
+__device__ __forceinline__ void fft_ct(C (&v)[E], C* sm, int t, int seq, const ux_of<C>* __restrict__ tw) {
   constexpr CtPlan P = ct_plan(L);
   constexpr int Tc = L / E;
   static_for<0, P.nst>([&](auto s_) {

@@ -57,6 +57,8 @@ template <typename T> static YTab<T> build_ytab() {
   for (int i = 0; i < kLdim * kLdim; i++) {
     t.A[i] = T(0);
     t.B[i] = T(0);
+    t.Al[i] = T(0);
+    t.Bl[i] = T(0);
   }
   for (int a = 0; a < kLdim; a++) t.c[a] = T(c[a]);
   for (int l = 1; l < kLdim; l++) {
@@ -66,6 +68,10 @@ template <typename T> static YTab<T> build_ytab() {
       const double B = num > 0 ? std::sqrt(num / (4.0 * (l - 1) * (l - 1) - 1.0)) : 0.0;
       t.A[l * kLdim + a] = T(A);
       t.B[l * kLdim + a] = T(B);
+      if (sizeof(T) == 4) {
+        t.Al[l * kLdim + a] = T(A - (double)T(A));
+        t.Bl[l * kLdim + a] = T(B - (double)T(B));
+      }
     }
   }
   return t;
@@ -78,6 +84,60 @@ template <> const YTab<float>& host_ytab<float>() {
 template <> const YTab<double>& host_ytab<double>() {
   static const YTab<double> t = build_ytab<double>();
   return t;
+}
+
+// ------------------------------------------------------------------ Y_lm(khat) table
+// One thread per stored mode (i, j, kz): khat in FP64, then for a = 0..l_max the recurrence in
+// l (FP64 coefficients) and (x + i y)^a; each Y_{l,m} of an even l >= 2 is stored rounded to
+// FP32 at ytab[(ytab_base(l) + h) * modes + (i N + j) NH + kz] (h = 0, 2a-1, 2a for m = 0,
+// +a, -a). The mode k = 0 gets 0.
+__global__ void __launch_bounds__(256) k_ytab_build(float* __restrict__ ytab, int N, int ell_max,
+                                                    const __grid_constant__ YTab<double> yt) {
+  const int NH = N / 2;
+  const int64_t modes = (int64_t)N * N * NH;
+  const double sq2 = 1.41421356237309504880;
+  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < modes; m += (int64_t)gridDim.x * blockDim.x) {
+    const int kz = (int)(m % NH);
+    const int64_t ij = m / NH;
+    const int j = (int)(ij % N), i = (int)(ij / N);
+    const double fx = i < NH ? i : i - N, fy = j < NH ? j : j - N, fz = kz;
+    const double r2 = fx * fx + fy * fy + fz * fz;
+    const double inv = r2 > 0.0 ? 1.0 / sqrt(r2) : 0.0;
+    const double x = fx * inv, y = fy * inv, z = fz * inv;
+    double pr = 1.0, pi = 0.0;  // (x + i y)^a
+    for (int a = 0; a <= ell_max; a++) {
+      double qm1 = 0.0, qm2 = 0.0;
+      for (int l = a; l <= ell_max; l++) {
+        double q;
+        if (l == a)
+          q = yt.c[a];
+        else if (l == a + 1)
+          q = yt.A[l * kLdim + a] * z * qm1;
+        else
+          q = yt.A[l * kLdim + a] * (z * qm1 - yt.B[l * kLdim + a] * qm2);
+        qm2 = qm1;
+        qm1 = q;
+        if (l < 2 || (l & 1)) continue;
+        float* base = ytab + (int64_t)ytab_base(l) * modes + m;
+        if (r2 == 0.0) {
+          if (a == 0) base[0] = 0.f;
+          else base[(int64_t)(2 * a - 1) * modes] = base[(int64_t)(2 * a) * modes] = 0.f;
+        } else if (a == 0) {
+          base[0] = (float)q;
+        } else {
+          base[(int64_t)(2 * a - 1) * modes] = (float)(sq2 * q * pr);
+          base[(int64_t)(2 * a) * modes] = (float)(sq2 * q * pi);
+        }
+      }
+      const double nr = pr * x - pi * y;
+      pi = pr * y + pi * x;
+      pr = nr;
+    }
+  }
+}
+
+void launch_ytab_build(float* ytab, int N, int ell_max, int nsm, cudaStream_t s) {
+  k_ytab_build<<<8 * nsm, 256, 0, s>>>(ytab, N, ell_max, host_ytab<double>());
 }
 
 // ------------------------------------------------------------------ dispatch

@@ -33,27 +33,31 @@ template <int N> struct Shape {
   static constexpr int ZT = ROWS * Tz;   // threads of a row block
 };
 
-template <typename T> constexpr int min_blocks(int threads) {
-  return sizeof(T) == 4 ? (threads >= 512 ? 2 : (threads >= 256 ? 3 : 4)) : 1;
+// Resident blocks per SM the register allocation must allow. Threads holding 24 complex
+// elements (3 * 2^a meshes) get at least 128 registers in FP32; 8 elements fit in 64.
+template <typename T, int E> constexpr int min_blocks(int threads) {
+  if constexpr (sizeof(T) != 4) return 1;
+  if constexpr (E > 8) return threads >= 512 ? 1 : 65536 / (((threads + 31) / 32) * 32 * 128);
+  return threads >= 512 ? 2 : (threads >= 256 ? 3 : 4);
 }
 
 template <int N> __device__ __forceinline__ int sfreq(int i) { return i < N / 2 ? i : i - N; }
 
 // r2c unpack: X[k] = (Z[k] + Z*[L-k])/2 - i/2 w^k (Z[k] - Z*[L-k]), w = exp(-2 pi i/N)
 template <typename C, typename T>
-__device__ __forceinline__ C r2c_unpack(C zk, C zm, C w) {
+__device__ __forceinline__ C r2c_unpack(C zk, C zm, ux<T> w) {
   const C zc = cconj(zm);
   const C e = cscale(cadd(zk, zc), T(0.5));
   const C d = csub(zk, zc);
   const C o = mk(T(0.5) * d.y, T(-0.5) * d.x);
-  return cadd(e, cmul(w, o));
+  return cadd(e, umul(o, w));
 }
 
 // ------------------------------------------------------------------ pass z: r2c of plain rows
 template <typename T, int N>
-__global__ void __launch_bounds__(Shape<N>::ZT, min_blocks<T>(Shape<N>::ZT))
-    k_r2c_z(const T* __restrict__ in, cx<T>* __restrict__ out, const cx<T>* __restrict__ twh,
-            const cx<T>* __restrict__ twr) {
+__global__ void __launch_bounds__(Shape<N>::ZT, min_blocks<T, Shape<N>::E>(Shape<N>::ZT))
+    k_r2c_z(const T* __restrict__ in, cx<T>* __restrict__ out, const ux<T>* __restrict__ twh,
+            const ux<T>* __restrict__ twr) {
   using C = cx<T>;
   using S = Shape<N>;
   constexpr int L = S::NH, E = S::E, Tc = S::Tz;
@@ -74,16 +78,16 @@ __global__ void __launch_bounds__(Shape<N>::ZT, min_blocks<T>(Shape<N>::ZT))
   for (int e = 0; e < E; e++) {
     const int k = t + Tc * e;
     const C zm = sm[sidx<kPaddedRows, L, 1>(r, k ? L - k : 0)];
-    dst[k] = r2c_unpack<C, T>(v[e], zm, ldg_c(twr + k));
+    dst[k] = r2c_unpack<C, T>(v[e], zm, ldg_u(twr + k));
   }
 }
 
 // ------------------------------------------------------------------ pass z: c2r
 // Rows of L stored modes (the kz = N/2 mode taken as 0) -> N reals, times `scale`.
 template <typename T, int N>
-__global__ void __launch_bounds__(Shape<N>::ZT, min_blocks<T>(Shape<N>::ZT))
-    k_c2r_z(const cx<T>* __restrict__ in, T* __restrict__ out, const cx<T>* __restrict__ twh,
-            const cx<T>* __restrict__ twr, T scale) {
+__global__ void __launch_bounds__(Shape<N>::ZT, min_blocks<T, Shape<N>::E>(Shape<N>::ZT))
+    k_c2r_z(const cx<T>* __restrict__ in, T* __restrict__ out, const ux<T>* __restrict__ twh,
+            const ux<T>* __restrict__ twr, T scale) {
   using C = cx<T>;
   using S = Shape<N>;
   constexpr int L = S::NH, E = S::E, Tc = S::Tz;
@@ -99,7 +103,7 @@ __global__ void __launch_bounds__(Shape<N>::ZT, min_blocks<T>(Shape<N>::ZT))
     const C xk = src[k];
     const C xm = k ? cconj(src[L - k]) : mk(T(0), T(0));
     const C ev = cscale(cadd(xk, xm), T(0.5));
-    const C od = cmul(cscale(csub(xk, xm), T(0.5)), cconj(ldg_c(twr + k)));
+    const C od = umul(cscale(csub(xk, xm), T(0.5)), uconj(ldg_u(twr + k)));
     v[e] = mk(ev.x - od.y, ev.y + od.x);  // E + i O
   }
   fft_ct<C, E, L, kPaddedRows, 1, +1>(v, sm, t, r, twh);
@@ -117,7 +121,7 @@ __global__ void __launch_bounds__(Shape<N>::ZT, min_blocks<T>(Shape<N>::ZT))
 template <typename T, int N>
 __global__ void __launch_bounds__(512) k_ylm_r2c_z(const T* __restrict__ f, cx<T>* __restrict__ out,
                                                   int64_t spec_stride, int ell, int h0, int M,
-                                                  const cx<T>* __restrict__ twh, const cx<T>* __restrict__ twr,
+                                                  const ux<T>* __restrict__ twh, const ux<T>* __restrict__ twr,
                                                   const T* __restrict__ axis, int rows,
                                                   const __grid_constant__ YTab<T> yt) {
   using C = cx<T>;
@@ -142,7 +146,7 @@ __global__ void __launch_bounds__(512) k_ylm_r2c_z(const T* __restrict__ f, cx<T
         for (int s = 0; s < M; s++) stage[(s * rows + r) * N + kk] = T(0);
         continue;
       }
-      const T inv = rsqrt_t<T>(r2);
+      const T inv = rsqrt_fast<T>(r2);
       const T x = vx * inv, y = vy * inv, z = vz * inv;
       T pr = T(1), pi = T(0);
       for (int s = 0; s < a_lo; s++) {
@@ -151,7 +155,7 @@ __global__ void __launch_bounds__(512) k_ylm_r2c_z(const T* __restrict__ f, cx<T
         pr = nr;
       }
       for (int a = a_lo; a <= a_hi; a++) {
-        const T q = fv * ylm_q<T>(yt, ell, a, z);
+        const T q = fv * ylm_q<T, false>(yt, ell, a, z);
         if (a == 0) {
           stage[r * N + kk] = q;
         } else {
@@ -182,15 +186,15 @@ __global__ void __launch_bounds__(512) k_ylm_r2c_z(const T* __restrict__ f, cx<T
   for (int e = 0; e < E; e++) {
     const int k = t + Tc * e;
     const C zm = xb[sidx<kPaddedRows, L, 1>(sq, k ? L - k : 0)];
-    dst[k] = r2c_unpack<C, T>(v[e], zm, ldg_c(twr + k));
+    dst[k] = r2c_unpack<C, T>(v[e], zm, ldg_u(twr + k));
   }
 }
 
 // ------------------------------------------------------------------ pass y (in place)
 // Block: one (i, kz-tile) slab, TW columns x Tc threads (column fastest).
 template <typename T, int N, int DIR, int TW>
-__global__ void __launch_bounds__(TW * Shape<N>::Tc, min_blocks<T>(TW * Shape<N>::Tc))
-    k_fft_y(cx<T>* __restrict__ data, int64_t spec_stride, const cx<T>* __restrict__ twf) {
+__global__ void __launch_bounds__(TW * Shape<N>::Tc, min_blocks<T, Shape<N>::E>(TW * Shape<N>::Tc))
+    k_fft_y(cx<T>* __restrict__ data, int64_t spec_stride, const ux<T>* __restrict__ twf) {
   using C = cx<T>;
   using S = Shape<N>;
   constexpr int NH = S::NH, E = S::E, Tc = S::Tc;
@@ -210,8 +214,8 @@ __global__ void __launch_bounds__(TW * Shape<N>::Tc, min_blocks<T>(TW * Shape<N>
 
 // ------------------------------------------------------------------ pass x (plain)
 template <typename T, int N, int DIR>
-__global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T>(Shape<N>::CT))
-    k_fft_x(const cx<T>* in, cx<T>* out, const cx<T>* __restrict__ twf) {
+__global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T, Shape<N>::E>(Shape<N>::CT))
+    k_fft_x(const cx<T>* in, cx<T>* out, const ux<T>* __restrict__ twf) {
   using C = cx<T>;
   using S = Shape<N>;
   constexpr int NH = S::NH, E = S::E, Tc = S::Tc, TW = S::TW;
@@ -235,9 +239,9 @@ __global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T>(Shape<N>::CT))
 // where some n_d = -N/2 when the inverse transform follows; stored as F0.
 // Binned: sum over modes of mult |X|^2 (slot SLOT_P0). Persistent over tiles.
 template <typename T, int N>
-__global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T>(Shape<N>::CT))
-    k_combine_x(const cx<T>* B, cx<T>* F0, const cx<T>* __restrict__ twf, int interlaced, int compensate,
-                int roundtrip, const cx<T>* __restrict__ phase, const T* __restrict__ invw, BinArgs ba) {
+__global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T, Shape<N>::E>(Shape<N>::CT))
+    k_combine_x(const cx<T>* B, cx<T>* F0, const ux<T>* __restrict__ twf, int interlaced, int compensate,
+                int roundtrip, const ux<T>* __restrict__ phase, const cx<T>* __restrict__ invw, BinArgs ba) {
   using C = cx<T>;
   using S = Shape<N>;
   constexpr int NH = S::NH, E = S::E, Tc = S::Tc, TW = S::TW;
@@ -262,8 +266,9 @@ __global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T>(Shape<N>::CT))
     for (int e = 0; e < E; e++) v[e] = B[off + (t + Tc * e) * si];
     fft_ct<C, E, N, kInterleaved, TW, -1>(v, sm, t, c, twf);
     const int ny = sfreq<N>(j);
-    const C phy = ldg_c(phase + j), phz = ldg_c(phase + N + kz);
-    const T wyz = invw[j] * invw[N + kz];
+    const C iwy = ldg_c(invw + j), iwz = ldg_c(invw + N + kz);
+    const T wyz = iwy.x * iwz.x, lyz = iwy.y + iwz.y;
+    const int syz = sfreq<N>(j) + kz + 3 * N / 2;  // index of exp(-i pi (nx + ny + nz) / N) less nx
     const T mult = kz ? T(2) : T(1);
 #pragma unroll
     for (int e = 0; e < E; e++) {
@@ -272,10 +277,16 @@ __global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T>(Shape<N>::CT))
       C X = v[e];
       if (interlaced) {
         const C A = F0[addr];
-        const C ph = cmul(cmul(ldg_c(phase + ii), phy), phz);
-        X = cscale(cadd(A, cmul(ph, X)), T(0.5));
+        X = cscale(cadd(A, umul(X, ldg_u(phase + syz + sfreq<N>(ii)))), T(0.5));
       }
-      if (compensate) X = cscale(X, invw[ii] * wyz);
+      if (compensate) {
+        // 1/W = prod_d hi_d (1 + lo_d): the relative rounding errors lo_d of the per-axis
+        // factors enter the roundings of the products X * w3, so that no per-axis
+        // deterministic error is left on the modes
+        const C iwx = ldg_c(invw + ii);
+        const T w3 = iwx.x * wyz, l3 = iwx.y + lyz;
+        X = mk(fma_t(X.x, w3, X.x * w3 * l3), fma_t(X.y, w3, X.y * w3 * l3));
+      }
       const bool nyq = (ii == N / 2) || (j == N / 2);
       if (roundtrip && nyq) X = mk(T(0), T(0));
       F0[addr] = X;
@@ -297,10 +308,11 @@ __global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T>(Shape<N>::CT))
 // Per tile: F0 once (kept in shared memory, each thread its own modes); for each harmonic h
 // of the group, the x-pass of G_h and acc += Y_{l,m(h)}(khat) Re[G_h conj(F0)] per mode;
 // then mult * acc into the bins of `slot`.
-template <typename T, int N>
-__global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T>(Shape<N>::CT))
+template <typename T, int N, bool YT>
+__global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T, Shape<N>::E>(Shape<N>::CT))
     k_bin_x(const cx<T>* G, int64_t spec_stride, int ell, int h0, int M, const cx<T>* __restrict__ F0,
-            const cx<T>* __restrict__ twf, int slot, BinArgs ba, const __grid_constant__ YTab<T> yt) {
+            const ux<T>* __restrict__ twf, int slot, BinArgs ba, const float* __restrict__ ytab,
+            const __grid_constant__ YTab<T> yt) {
   using C = cx<T>;
   using S = Shape<N>;
   constexpr int NH = S::NH, E = S::E, Tc = S::Tc, TW = S::TW;
@@ -334,26 +346,37 @@ __global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T>(Shape<N>::CT))
       const int h = h0 + s;
       const int a = harm_a(h), sg = harm_sign(h);
       const C* Gs = G + (int64_t)s * spec_stride;
+      // FP32 with a table: Y_lm(khat) of this harmonic, same mode layout as the spectra
+      const float* Ys = YT ? ytab + (int64_t)(ytab_base(ell) + h) * (si * N) + off : nullptr;
       C v[E];
+      float yv[YT ? E : 1];  // table values, loaded with the spectrum so that the FFT hides their latency
 #pragma unroll
-      for (int e = 0; e < E; e++) v[e] = Gs[off + (t + Tc * e) * si];
+      for (int e = 0; e < E; e++) {
+        v[e] = Gs[off + (t + Tc * e) * si];
+        if constexpr (YT) yv[e] = __ldg(Ys + (t + Tc * e) * si);
+      }
       fft_ct<C, E, N, kInterleaved, TW, -1>(v, sm, t, c, twf);
 #pragma unroll
       for (int e = 0; e < E; e++) {
         const T fx = T(sfreq<N>(t + Tc * e));
         const T r2 = fx * fx + r2yz;
         if (r2 == T(0)) continue;
-        const T inv = rsqrt_t<T>(r2);
-        const T x = fx * inv, y = fy * inv;
-        T Y = ylm_q<T>(yt, ell, a, fz * inv);
-        if (a > 0) {
-          T pr = x, pi = y;
-          for (int u = 1; u < a; u++) {
-            const T nr = pr * x - pi * y;
-            pi = pr * y + pi * x;
-            pr = nr;
+        T Y;
+        if constexpr (YT) {
+          Y = (T)yv[e];
+        } else {
+          const T inv = rsqrt_t<T>(r2);
+          const T x = fx * inv, y = fy * inv;
+          Y = ylm_q<T>(yt, ell, a, fz * inv);
+          if (a > 0) {
+            T pr = x, pi = y;
+            for (int u = 1; u < a; u++) {
+              const T nr = pr * x - pi * y;
+              pi = pr * y + pi * x;
+              pr = nr;
+            }
+            Y = sq2 * Y * (sg > 0 ? pr : pi);
           }
-          Y = sq2 * Y * (sg > 0 ? pr : pi);
         }
         const C fv = sF0[(t + Tc * e) * TW + c];
         acc[e] += Y * (v[e].x * fv.x + v[e].y * fv.y);
@@ -386,18 +409,19 @@ template <typename K> static void set_smem(K kernel, size_t bytes) {
 
 template <typename T, int N> struct Passes {
   using C = cx<T>;
+  using U = ux<T>;
   using S = Shape<N>;
   static size_t smem_col() { return (size_t)N * S::TW * sizeof(C); }
   static size_t smem_bins(int nk) { return (size_t)nk * sizeof(double) + (size_t)((S::CT + 31) / 32) * nk * sizeof(T); }
   static size_t smem_combine(int nk) { return smem_col() + smem_bins(nk); }
   static size_t smem_bin(int nk) { return 2 * smem_col() + smem_bins(nk); }
 
-  static void r2c_z(const T* in, C* out, const C* twh, const C* twr, cudaStream_t s) {
+  static void r2c_z(const T* in, C* out, const U* twh, const U* twr, cudaStream_t s) {
     const size_t smem = (size_t)S::ROWS * padded_len(S::NH) * sizeof(C);
     set_smem(k_r2c_z<T, N>, smem);
     k_r2c_z<T, N><<<N * N / S::ROWS, S::ZT, smem, s>>>(in, out, twh, twr);
   }
-  static void c2r_z(const C* in, T* out, const C* twh, const C* twr, T scale, cudaStream_t s) {
+  static void c2r_z(const C* in, T* out, const U* twh, const U* twr, T scale, cudaStream_t s) {
     const size_t smem = (size_t)S::ROWS * padded_len(S::NH) * sizeof(C);
     set_smem(k_c2r_z<T, N>, smem);
     k_c2r_z<T, N><<<N * N / S::ROWS, S::ZT, smem, s>>>(in, out, twh, twr, scale);
@@ -407,7 +431,7 @@ template <typename T, int N> struct Passes {
     const size_t xb = (size_t)M * rows * padded_len(S::NH) * sizeof(C);
     return stage > xb ? stage : xb;
   }
-  static void ylm_z(const T* f, C* out, int64_t stride, int ell, int h0, int M, const C* twh, const C* twr,
+  static void ylm_z(const T* f, C* out, int64_t stride, int ell, int h0, int M, const U* twh, const U* twr,
                     const T* axis, int rows, cudaStream_t s) {
     const size_t smem = smem_ylm(M, rows);
     set_smem(k_ylm_r2c_z<T, N>, smem);
@@ -415,7 +439,7 @@ template <typename T, int N> struct Passes {
                                                                     host_ytab<T>());
   }
   // variant 0: TW columns per block; variant 1: TW/2 (half the threads and shared memory)
-  template <int TWV> static void fft_y_tw(C* data, int64_t stride, int nspec, const C* twf, int dir, cudaStream_t s) {
+  template <int TWV> static void fft_y_tw(C* data, int64_t stride, int nspec, const U* twf, int dir, cudaStream_t s) {
     const size_t smem = (size_t)N * TWV * sizeof(C);
     dim3 grid(N * (S::NH / TWV), nspec);
     if (dir < 0) {
@@ -426,14 +450,14 @@ template <typename T, int N> struct Passes {
       k_fft_y<T, N, 1, TWV><<<grid, TWV * S::Tc, smem, s>>>(data, stride, twf);
     }
   }
-  static void fft_y(C* data, int64_t stride, int nspec, const C* twf, int dir, int variant, cudaStream_t s) {
+  static void fft_y(C* data, int64_t stride, int nspec, const U* twf, int dir, int variant, cudaStream_t s) {
     constexpr int TW2 = S::TW > 1 ? S::TW / 2 : 1;
     if (variant == 1 && S::TW > 1)
       fft_y_tw<TW2>(data, stride, nspec, twf, dir, s);
     else
       fft_y_tw<S::TW>(data, stride, nspec, twf, dir, s);
   }
-  static void fft_x(const C* in, C* out, const C* twf, int dir, cudaStream_t s) {
+  static void fft_x(const C* in, C* out, const U* twf, int dir, cudaStream_t s) {
     const size_t smem = smem_col();
     const unsigned grid = N * (S::NH / S::TW);
     if (dir < 0) {
@@ -444,17 +468,22 @@ template <typename T, int N> struct Passes {
       k_fft_x<T, N, 1><<<grid, S::CT, smem, s>>>(in, out, twf);
     }
   }
-  static void combine_x(const C* B, C* F0, const C* twf, int interlaced, int compensate, int roundtrip,
-                        const C* phase, const T* invw, const BinArgs& ba, int ctas, cudaStream_t s) {
+  static void combine_x(const C* B, C* F0, const U* twf, int interlaced, int compensate, int roundtrip,
+                        const U* phase, const C* invw, const BinArgs& ba, int ctas, cudaStream_t s) {
     const size_t smem = smem_combine(ba.nk);
     set_smem(k_combine_x<T, N>, smem);
     k_combine_x<T, N><<<ctas, S::CT, smem, s>>>(B, F0, twf, interlaced, compensate, roundtrip, phase, invw, ba);
   }
-  static void bin_x(const C* G, int64_t stride, int ell, int h0, int M, const C* F0, const C* twf, int slot,
-                    const BinArgs& ba, int ctas, cudaStream_t s) {
+  static void bin_x(const C* G, int64_t stride, int ell, int h0, int M, const C* F0, const U* twf, int slot,
+                    const BinArgs& ba, int ctas, const float* ytab, cudaStream_t s) {
     const size_t smem = smem_bin(ba.nk);
-    set_smem(k_bin_x<T, N>, smem);
-    k_bin_x<T, N><<<ctas, S::CT, smem, s>>>(G, stride, ell, h0, M, F0, twf, slot, ba, host_ytab<T>());
+    if (ytab && sizeof(T) == 4) {
+      set_smem(k_bin_x<T, N, true>, smem);
+      k_bin_x<T, N, true><<<ctas, S::CT, smem, s>>>(G, stride, ell, h0, M, F0, twf, slot, ba, ytab, host_ytab<T>());
+    } else {
+      set_smem(k_bin_x<T, N, false>, smem);
+      k_bin_x<T, N, false><<<ctas, S::CT, smem, s>>>(G, stride, ell, h0, M, F0, twf, slot, ba, ytab, host_ytab<T>());
+    }
   }
   static int ctas(int which, int nk, int nsm) {
     int per = 0;
@@ -464,8 +493,8 @@ template <typename T, int N> struct Passes {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_combine_x<T, N>, S::CT, smem);
     } else {
       const size_t smem = smem_bin(nk);
-      set_smem(k_bin_x<T, N>, smem);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bin_x<T, N>, S::CT, smem);
+      set_smem(k_bin_x<T, N, false>, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bin_x<T, N, false>, S::CT, smem);
     }
     if (per < 1) per = 1;
     const int ntiles = N * (S::NH / S::TW);

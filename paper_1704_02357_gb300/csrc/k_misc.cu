@@ -43,6 +43,39 @@ __device__ __forceinline__ double fkp_w(const PaintArgs& a, double nb) {
   return a.nbar ? (a.P0 > 0.0 ? 1.0 / (1.0 + nb * a.P0) : 1.0) : a.wf_default;
 }
 
+// The FP32 mesh value of one particle: v rounded down or up to a neighbouring float, chosen
+// by a hash of (particle, catalog) with the probabilities that make its expectation v. All
+// particles of a catalog with constant weights share one v; rounded to nearest, its error
+// would scale that catalog's whole field, survey window included, and at the lowest k the
+// randoms' window exceeds the data-minus-randoms field by two orders of magnitude. Dithered,
+// the rounding errors are independent across particles and only add white noise ~1e-7 of the
+// shot noise. The hash is the 32-bit finaliser of MurmurHash3 (Appleby) applied to the
+// particle index mixed with a per-catalog salt.
+struct Dither {
+  float lo, hi;    // the two floats around v (equal when v is a float)
+  uint32_t thr;    // P(hi) * 2^32
+};
+__device__ __forceinline__ Dither dither_of(double v) {
+  Dither d;
+  d.lo = (float)v;
+  const double r = v - (double)d.lo;
+  d.hi = r == 0.0 ? d.lo : nextafterf(d.lo, r > 0.0 ? INFINITY : -INFINITY);
+  const double p = r == 0.0 ? 0.0 : r / ((double)d.hi - (double)d.lo);  // in [0, 1/2]
+  d.thr = (uint32_t)(p * 4294967296.0);
+  return d;
+}
+__device__ __forceinline__ uint32_t mix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+__device__ __forceinline__ float dither_pick(const Dither& d, int64_t p, int is_randoms) {
+  const uint32_t key = (uint32_t)p ^ ((uint32_t)(p >> 32) * 0x9e3779b9u) ^ (is_randoms ? 0x5bd1e995u : 0u);
+  return mix32(key) < d.thr ? d.hi : d.lo;
+}
 // Catalog fields from the device descriptor of the current mock, when the arguments carry one.
 __device__ __forceinline__ PaintArgs resolve(const PaintArgs& in) {
   PaintArgs a = in;
@@ -243,7 +276,8 @@ __global__ void __launch_bounds__(256) k_paint(PaintArgs a_in, int is_randoms, d
   const PaintArgs a = resolve(a_in);
   const double sign = is_randoms == 1 ? -derived[D_ALPHA] : 1.0;
   const bool uniform = (a.weight == nullptr) && (a.nbar == nullptr);
-  const T v_uniform = (T)(sign * a.wf_default);
+  const double v_uniform = sign * a.wf_default;
+  const Dither d_uniform = dither_of(v_uniform);
   const double lim = (double)N;
   unsigned bad = 0, out = 0;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.count;
@@ -262,7 +296,11 @@ __global__ void __launch_bounds__(256) k_paint(PaintArgs a_in, int is_randoms, d
       continue;
     }
     if (ux < 0.0 || ux >= lim || uy < 0.0 || uy >= lim || uz < 0.0 || uz >= lim) out++;
-    const T v = uniform ? v_uniform : (T)(sign * wc * fkp_w(a, nb));
+    T v;
+    if constexpr (sizeof(T) == 4)
+      v = dither_pick(uniform ? d_uniform : dither_of(sign * wc * fkp_w(a, nb)), p, is_randoms);
+    else
+      v = sign * wc * fkp_w(a, nb);
     int ix[3], iy[3], iz[3];
     T wx[3], wy[3], wz[3];
     if constexpr (sizeof(T) == 4) {
@@ -341,7 +379,8 @@ __global__ void __launch_bounds__(256) k_ptile_prep(PaintArgs a_in, int is_rando
   const PaintArgs a = resolve(a_in);
   const double sign = is_randoms == 1 ? -derived[D_ALPHA] : 1.0;
   const bool uniform = (a.weight == nullptr) && (a.nbar == nullptr);
-  const float v_uniform = (float)(sign * a.wf_default);
+  const double v_uniform = sign * a.wf_default;
+  const Dither d_uniform = dither_of(v_uniform);
   const double lim = (double)N;
   const int nts = N / kPT;
   unsigned bad = 0, out = 0;
@@ -363,7 +402,7 @@ __global__ void __launch_bounds__(256) k_ptile_prep(PaintArgs a_in, int is_rando
       continue;
     }
     if (u[0] < 0.0 || u[0] >= lim || u[1] < 0.0 || u[1] >= lim || u[2] < 0.0 || u[2] >= lim) out++;
-    const float v = uniform ? v_uniform : (float)(sign * wc * fkp_w(a, nb));
+    const float v = dither_pick(uniform ? d_uniform : dither_of(sign * wc * fkp_w(a, nb)), p, is_randoms);
     unsigned packed[3];
     int tc[3];
     for (int d = 0; d < 3; d++) {

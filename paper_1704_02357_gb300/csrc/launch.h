@@ -115,18 +115,29 @@ constexpr int z_rows(int N) {
   return r;
 }
 
+// Twiddle and phase tables hold ux<T> entries (FP32: {cos, sin, 1/|w| - 1, 0}); the
+// compensation table holds cx<T> {1/W_d rounded, its relative rounding error}.
+// Y_lm(khat) table of the FP32 binning pass: harmonic slots of l = 2, 4, ..., l_max in order,
+// 2l+1 each (h order of the harmonics), every slot one value per stored mode [i][j][kz].
+__host__ __device__ constexpr int ytab_base(int ell) {
+  int b = 0;
+  for (int l = 2; l < ell; l += 2) b += 2 * l + 1;
+  return b;
+}
+void launch_ytab_build(float* ytab, int N, int ell_max, int nsm, cudaStream_t s);
+
 template <typename T> struct PassTable {
   int N, E, tw, rows_z, tz;
-  void (*r2c_z)(const T*, cx<T>*, const cx<T>*, const cx<T>*, cudaStream_t);
-  void (*c2r_z)(const cx<T>*, T*, const cx<T>*, const cx<T>*, T, cudaStream_t);
-  void (*ylm_z)(const T*, cx<T>*, int64_t, int, int, int, const cx<T>*, const cx<T>*, const T*, int, cudaStream_t);
+  void (*r2c_z)(const T*, cx<T>*, const ux<T>*, const ux<T>*, cudaStream_t);
+  void (*c2r_z)(const cx<T>*, T*, const ux<T>*, const ux<T>*, T, cudaStream_t);
+  void (*ylm_z)(const T*, cx<T>*, int64_t, int, int, int, const ux<T>*, const ux<T>*, const T*, int, cudaStream_t);
   size_t (*smem_ylm)(int, int);
-  void (*fft_y)(cx<T>*, int64_t, int, const cx<T>*, int, int, cudaStream_t);  // ..., dir, tile variant
-  void (*fft_x)(const cx<T>*, cx<T>*, const cx<T>*, int, cudaStream_t);
-  void (*combine_x)(const cx<T>*, cx<T>*, const cx<T>*, int, int, int, const cx<T>*, const T*, const BinArgs&, int,
-                    cudaStream_t);
-  void (*bin_x)(const cx<T>*, int64_t, int, int, int, const cx<T>*, const cx<T>*, int, const BinArgs&, int,
-                cudaStream_t);
+  void (*fft_y)(cx<T>*, int64_t, int, const ux<T>*, int, int, cudaStream_t);  // ..., dir, tile variant
+  void (*fft_x)(const cx<T>*, cx<T>*, const ux<T>*, int, cudaStream_t);
+  void (*combine_x)(const cx<T>*, cx<T>*, const ux<T>*, int, int, int, const ux<T>*, const cx<T>*, const BinArgs&,
+                    int, cudaStream_t);
+  void (*bin_x)(const cx<T>*, int64_t, int, int, int, const cx<T>*, const ux<T>*, int, const BinArgs&, int,
+                const float*, cudaStream_t);  // ..., Y_lm(khat) table or nullptr
   int (*ctas)(int, int, int);  // (which: 0 combine, 1 bin; nk; SM count) -> persistent blocks
   size_t (*smem_combine)(int);
   size_t (*smem_bin)(int);

@@ -52,6 +52,8 @@ struct Plan {
   size_t Sr, Sc;
   int n2max;
   // workspace offsets
+  bool has_ytab = false;
+  size_t ytab_bytes = 0, o_ytab = 0;
   size_t o_mesh1, o_mesh2, o_f0, o_w, o_f, o_g, o_twh, o_twf, o_twr, o_axis, o_phase, o_invw, o_bin, o_kmag, o_cnt,
       o_lo, o_hi, o_nmodes, o_ksum, o_sums, o_derived, o_bins, o_out, o_tcnt, o_toff, o_tcur, o_prec, o_ptile,
       o_psort, total;
@@ -74,6 +76,7 @@ pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl,
   if (!(std::isfinite(p->P0) && p->P0 >= 0) || !(std::isfinite(p->nbar) && p->nbar >= 0)) { *why = "P0 and nbar must be finite and >= 0"; return PSPEC_EINVAL; }
   if (max_kbins < 1 || max_kbins > PSPEC_MAX_KBINS) { *why = "max_kbins out of range"; return PSPEC_EINVAL; }
   if (p->max_group_bytes < 0) { *why = "max_group_bytes < 0"; return PSPEC_EINVAL; }
+  if (p->ylm_table != 0 && p->ylm_table != -1) { *why = "ylm_table must be 0 or -1"; return PSPEC_EINVAL; }
   if (p->max_particles < 0 || p->max_particles > (int64_t)0xfffffff0) { *why = "max_particles out of range"; return PSPEC_EINVAL; }
 
   const bool f64 = p->precision == PSPEC_FP64;
@@ -126,12 +129,17 @@ pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl,
   pl->o_w = take(pl->Sc);
   pl->o_f = pl->roundtrip ? take(pl->Sr) : 0;
   pl->o_g = pl->group_max ? take(pl->Sc * pl->group_max) : 0;
-  pl->o_twh = take(NH * csz);
-  pl->o_twf = take(N * csz);
-  pl->o_twr = take(NH * csz);
+  const size_t usz = 16;  // one table factor: float4 or double2
+  pl->o_twh = take(NH * usz);
+  pl->o_twf = take(N * usz);
+  pl->o_twr = take(NH * usz);
   pl->o_axis = take(3 * (size_t)N * pl->esz);
-  pl->o_phase = take((N + NH) * csz);
-  pl->o_invw = take((N + NH) * (size_t)pl->esz);
+  pl->o_phase = take(3 * (size_t)N * usz);
+  pl->o_invw = take((N + NH) * csz);
+  // Y_lm(khat) of every stored mode for the FP32 binning pass (l = 2..l_max)
+  pl->ytab_bytes = (size_t)N * N * NH * sizeof(float) * (size_t)ytab_base(p->ell_max + 2);
+  pl->has_ytab = !f64 && p->ell_max >= 2 && p->ylm_table == 0 && pl->ytab_bytes <= (size_t)PSPEC_YLM_TABLE_AUTO_MAX;
+  pl->o_ytab = pl->has_ytab ? take(pl->ytab_bytes) : 0;
   pl->o_bin = take((pl->n2max + 1) * sizeof(int32_t));
   pl->o_kmag = take((pl->n2max + 1) * sizeof(double));
   pl->o_cnt = take((pl->n2max + 1) * sizeof(uint32_t));
@@ -253,23 +261,29 @@ pspec_status cuda_fail(Ctx* c, cudaError_t e, const char* what) {
   return PSPEC_ECUDA;
 }
 
+// exp(i a) as a table entry; in FP32 each component as hi + lo (lo = its rounding error).
+template <typename T> ux<T> unit_factor(double a);
+template <> ux<float> unit_factor<float>(double a) {
+  const double c = std::cos(a), s = std::sin(a);
+  const float ch = (float)c, sh = (float)s;
+  return make_float4(ch, sh, (float)(c - (double)ch), (float)(s - (double)sh));
+}
+template <> ux<double> unit_factor<double>(double a) { return make_double2(std::cos(a), std::sin(a)); }
+
 template <typename T>
 pspec_status upload_tables(Ctx* c) {
   const Plan& pl = c->pl;
   const int N = pl.g.N, NH = pl.g.NH;
   using C = cx<T>;
-  std::vector<C> twh(NH), twf(N), twr(NH), phase(N + NH);
-  std::vector<T> axis(3 * N), invw(N + NH);
+  using U = ux<T>;
+  std::vector<U> twh(NH), twf(N), twr(NH), phase(3 * N);
+  std::vector<C> invw(N + NH);
+  std::vector<T> axis(3 * N);
   for (int t = 0; t < NH; t++) {
-    const double a = -2.0 * M_PI * t / NH;
-    twh[t] = mk(T(std::cos(a)), T(std::sin(a)));
-    const double b = -2.0 * M_PI * t / N;
-    twr[t] = mk(T(std::cos(b)), T(std::sin(b)));
+    twh[t] = unit_factor<T>(-2.0 * M_PI * t / NH);
+    twr[t] = unit_factor<T>(-2.0 * M_PI * t / N);
   }
-  for (int t = 0; t < N; t++) {
-    const double a = -2.0 * M_PI * t / N;
-    twf[t] = mk(T(std::cos(a)), T(std::sin(a)));
-  }
+  for (int t = 0; t < N; t++) twf[t] = unit_factor<T>(-2.0 * M_PI * t / N);
   const double H = c->p.box_size / N;
   for (int d = 0; d < 3; d++)
     for (int i = 0; i < N; i++) axis[d * N + i] = T(c->p.box_corner[d] + i * H - c->p.observer[d]);
@@ -279,22 +293,26 @@ pspec_status upload_tables(Ctx* c) {
     const double x = M_PI * n / N;
     return std::pow(std::sin(x) / x, p);
   };
+  // exp(-i pi s / N), s = nx + ny + nz in [-3N/2, 3N/2): the H/2 shift of the second mesh
+  for (int i = 0; i < 3 * N; i++) phase[i] = unit_factor<T>(-M_PI * (i - 3 * N / 2) / N);
   for (int i = 0; i < N + NH; i++) {
     const int n = i < N ? (i < NH ? i : i - N) : (i - N);
-    const double a = -M_PI * n / N;  // exp(-i pi n / N): the H/2 shift of the second mesh
-    phase[i] = mk(T(std::cos(a)), T(std::sin(a)));
-    invw[i] = T(1.0 / sincp(n));
+    const double w = 1.0 / sincp(n);
+    const T hi = T(w);
+    invw[i] = mk(hi, T(w / (double)hi - 1.0));
   }
   cudaError_t e;
-  e = cudaMemcpyAsync(c->at<C>(pl.o_twh), twh.data(), NH * sizeof(C), cudaMemcpyHostToDevice, c->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(c->at<C>(pl.o_twf), twf.data(), N * sizeof(C), cudaMemcpyHostToDevice, c->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(c->at<C>(pl.o_twr), twr.data(), NH * sizeof(C), cudaMemcpyHostToDevice, c->stream);
+  e = cudaMemcpyAsync(c->at<U>(pl.o_twh), twh.data(), NH * sizeof(U), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->at<U>(pl.o_twf), twf.data(), N * sizeof(U), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->at<U>(pl.o_twr), twr.data(), NH * sizeof(U), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->at<T>(pl.o_axis), axis.data(), 3 * N * sizeof(T), cudaMemcpyHostToDevice, c->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(c->at<C>(pl.o_phase), phase.data(), (N + NH) * sizeof(C), cudaMemcpyHostToDevice, c->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(c->at<T>(pl.o_invw), invw.data(), (N + NH) * sizeof(T), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->at<U>(pl.o_phase), phase.data(), 3 * N * sizeof(U), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->at<C>(pl.o_invw), invw.data(), (N + NH) * sizeof(C), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->at<uint32_t>(pl.o_cnt), 0, (pl.n2max + 1) * sizeof(uint32_t), c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "table upload");
   TRY(run(c, PSPEC_K_OTHER, 0.0, [&] { launch_mode_counts(pl.g, c->at<uint32_t>(pl.o_cnt), c->nsm, c->stream); }));
+  if (pl.has_ytab)
+    TRY(run(c, PSPEC_K_OTHER, 0.0, [&] { launch_ytab_build(c->at<float>(pl.o_ytab), N, c->p.ell_max, c->nsm, c->stream); }));
   e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "table upload");
   return PSPEC_OK;
@@ -448,8 +466,17 @@ pspec_status do_paint(Ctx* c, const pspec_catalog* d, const pspec_catalog* r) {
   return PSPEC_OK;
 }
 
+// Range of the flattened harmonic list (see pspec_multipoles_range) a multipoles call covers.
+struct HRange {
+  int q0 = 0;
+  int q1 = 1 << 30;
+  bool include_p0 = true;
+  double* bins_out = nullptr;  // raw bins instead of finalized multipoles
+};
+
 template <typename T>
-pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, double* P, double* km, double* nm) {
+pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, double* P, double* km, double* nm,
+                           const HRange& hr = HRange()) {
   using C = cx<T>;
   const Plan& pl = c->pl;
   const Geo& g = pl.g;
@@ -462,12 +489,13 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
   C* W = c->at<C>(pl.o_w);
   T* f = pl.roundtrip ? c->at<T>(pl.o_f) : m1;
   C* G = c->at<C>(pl.o_g);
-  const C* twh = c->at<C>(pl.o_twh);
-  const C* twf = c->at<C>(pl.o_twf);
-  const C* twr = c->at<C>(pl.o_twr);
+  using U = ux<T>;
+  const U* twh = c->at<U>(pl.o_twh);
+  const U* twf = c->at<U>(pl.o_twf);
+  const U* twr = c->at<U>(pl.o_twr);
   const T* axis = c->at<T>(pl.o_axis);
-  const C* phase = c->at<C>(pl.o_phase);
-  const T* invw = c->at<T>(pl.o_invw);
+  const U* phase = c->at<U>(pl.o_phase);
+  const C* invw = c->at<C>(pl.o_invw);
   const double Sr = (double)pl.Sr, Sc = (double)pl.Sc;
   BinArgs ba;
   ba.bin_of_n2 = c->at<int32_t>(pl.o_bin);
@@ -512,16 +540,19 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
     transforms++;
   }
 
-  // a4 + a5: per multipole l >= 2, groups of harmonics
+  // a4 + a5: per multipole l >= 2, groups of harmonics (those of [q0, q1) of the flat list)
   int64_t sh = 0;
   const int64_t stride = (int64_t)N * N * g.NH;
+  int qbase = 0;
   for (int i = 0; i < n_ells; i++) {
     const int ell = ells[i];
     sh += 2 * ell + 1;
     if (ell == 0) continue;
     const int nh = 2 * ell + 1;
-    for (int h0 = 0; h0 < nh; h0 += pl.group_max) {
-      const int M = std::min(pl.group_max, nh - h0);
+    const int hlo = std::max(0, hr.q0 - qbase), hhi = std::min(nh, hr.q1 - qbase);
+    qbase += nh;
+    for (int h0 = hlo; h0 < hhi; h0 += pl.group_max) {
+      const int M = std::min(pl.group_max, hhi - h0);
       // z pass with the Y_lm weights: one block holds Ms harmonics x rows rows, tz threads each
       const int tz = PT->tz;
       const int ms_max = std::max(1, std::min(c->tune.ylm_harmonics, kYlmMaxThreads / tz));
@@ -534,11 +565,23 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
         }));
       }
       TRY(run(c, PSPEC_K_FFT_Y, acc(2 * M * Sc), [&] { PT->fft_y(G, stride, M, twf, -1, c->tune.tile_y, s); }));
-      TRY(run(c, PSPEC_K_BIN_X, acc(Sc + M * Sc), [&] {
-        PT->bin_x(G, stride, ell, h0, M, F0, twf, SLOT_ELL0 + i, ba, ctas_bin, s);
+      const float* ytab = pl.has_ytab ? c->at<float>(pl.o_ytab) : nullptr;
+      const double ybytes = ytab ? M * (double)N * N * g.NH * sizeof(float) : 0.0;
+      TRY(run(c, PSPEC_K_BIN_X, acc(Sc + M * Sc + ybytes), [&] {
+        PT->bin_x(G, stride, ell, h0, M, F0, twf, SLOT_ELL0 + i, ba, ctas_bin, ytab, s);
       }));
       transforms += M;
     }
+  }
+  if (hr.bins_out) {
+    const size_t nb = (size_t)(SLOT_ELL0 + n_ells) * nk * sizeof(double);
+    e = cudaMemcpyAsync(hr.bins_out, ba.bins, nb, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && !hr.include_p0) e = cudaMemsetAsync(hr.bins_out, 0, (size_t)nk * sizeof(double), s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "range bins");
+    c->transforms_last = transforms;
+    c->sh_last = sh;
+    c->bytes_mult = bytes;
+    return PSPEC_OK;
   }
   // a6
   TRY(run(c, PSPEC_K_FINAL, 0.0, [&] {
@@ -793,6 +836,45 @@ pspec_status pspec_multipoles_device(void* ctx, const int32_t* ells, int32_t n_e
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!P_dev || !k_mean_dev || !n_modes_dev) { c->err = "output pointers are NULL"; return PSPEC_EINVAL; }
   return multipoles_common(c, ells, n_ells, k_edges, n_kbins, P_dev, k_mean_dev, n_modes_dev);
+}
+
+pspec_status pspec_multipoles_range(void* ctx, const int32_t* ells, int32_t n_ells, const double* k_edges,
+                                    int32_t n_kbins, int32_t q0, int32_t q1, int32_t include_p0, double* bins) {
+  if (!ctx) return PSPEC_EINVAL;
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!bins || q0 < 0 || q1 < q0) { c->err = "bad harmonic range or NULL bins"; return PSPEC_EINVAL; }
+  TRY(check_ells_edges(c, ells, n_ells, k_edges, n_kbins));
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  TRY(upload_bins(c, k_edges, n_kbins));
+  HRange hr;
+  hr.q0 = q0;
+  hr.q1 = q1;
+  hr.include_p0 = include_p0 != 0;
+  hr.bins_out = bins;
+  double* out = c->at<double>(c->pl.o_out);
+  const int nk = n_kbins;
+  if (c->p.precision == PSPEC_FP64)
+    return do_multipoles<double>(c, ells, n_ells, nk, out + 2 * (size_t)nk, out, out + nk, hr);
+  return do_multipoles<float>(c, ells, n_ells, nk, out + 2 * (size_t)nk, out, out + nk, hr);
+}
+
+pspec_status pspec_finalize_bins(void* ctx, const double* bins, const int32_t* ells, int32_t n_ells,
+                                 const double* k_edges, int32_t n_kbins, double* P_dev, double* k_mean_dev,
+                                 double* n_modes_dev) {
+  if (!ctx) return PSPEC_EINVAL;
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!bins || !P_dev || !k_mean_dev || !n_modes_dev) { c->err = "NULL pointer"; return PSPEC_EINVAL; }
+  TRY(check_ells_edges(c, ells, n_ells, k_edges, n_kbins));
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  TRY(upload_bins(c, k_edges, n_kbins));
+  const Plan& pl = c->pl;
+  TRY(run(c, PSPEC_K_FINAL, 0.0, [&] {
+    launch_finalize(bins, c->at<double>(pl.o_nmodes), c->at<double>(pl.o_ksum), n_kbins, ells, n_ells,
+                    c->at<double>(pl.o_derived), P_dev, k_mean_dev, n_modes_dev, c->stream);
+  }));
+  return PSPEC_OK;
 }
 
 pspec_status pspec_set_randoms(void* ctx, const pspec_catalog* randoms) {
@@ -1054,6 +1136,7 @@ pspec_status pspec_get_plan_info(void* ctx, pspec_plan_info* info) {
   info->transforms_executed = c->transforms_last;
   info->kernel_launches = c->launches;
   info->model_bytes_last = c->bytes_paint + c->bytes_mult;
+  info->ylm_table_bytes = c->pl.has_ytab ? (int64_t)c->pl.ytab_bytes : 0;
   return PSPEC_OK;
 }
 

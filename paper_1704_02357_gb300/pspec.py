@@ -33,7 +33,7 @@ class Params(C.Structure):
                 ("compensate", C.c_int32), ("precision", C.c_int32), ("ell_max", C.c_int32),
                 ("box_size", C.c_double), ("box_corner", C.c_double * 3), ("observer", C.c_double * 3),
                 ("P0", C.c_double), ("nbar", C.c_double), ("max_group_bytes", C.c_int64),
-                ("max_particles", C.c_int64), ("cache_randoms", C.c_int32), ("reserved", C.c_int32)]
+                ("max_particles", C.c_int64), ("cache_randoms", C.c_int32), ("ylm_table", C.c_int32)]
 
 
 class Catalog(C.Structure):
@@ -56,7 +56,7 @@ class PlanInfo(C.Structure):
                 ("tile_y", C.c_int32), ("tile_x", C.c_int32), ("tile_bin", C.c_int32), ("rows_z", C.c_int32),
                 ("group_max", C.c_int32), ("bin_ctas", C.c_int32), ("sh_transforms", C.c_int64),
                 ("transforms_executed", C.c_int64), ("kernel_launches", C.c_int64),
-                ("model_bytes_last", C.c_double)]
+                ("model_bytes_last", C.c_double), ("ylm_table_bytes", C.c_int64)]
 
 
 _lib = None
@@ -92,6 +92,10 @@ SIGNATURES = [
     ("pspec_set_tuning", C.c_int32, [C.c_void_p, C.POINTER(Tuning)]),
     ("pspec_autotune", C.c_int32, [C.c_void_p, C.POINTER(Catalog), C.POINTER(Catalog), C.POINTER(C.c_int32),
                                    C.c_int32, C.POINTER(C.c_double), C.c_int32, C.c_int32, C.POINTER(Tuning)]),
+    ("pspec_multipoles_range", C.c_int32, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_double),
+                                           C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_void_p]),
+    ("pspec_finalize_bins", C.c_int32, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int32), C.c_int32,
+                                        C.POINTER(C.c_double), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("pspec_catalog_sums_noalloc", C.c_int32, [C.POINTER(Params), C.POINTER(Catalog), C.POINTER(Catalog), C.c_int32,
                                                C.c_void_p, C.c_void_p]),
 ]
@@ -156,7 +160,7 @@ class Estimator:
     def __init__(self, nmesh: int, box_size: float, box_corner, observer=(0.0, 0.0, 0.0), window="cic",
                  interlaced=False, compensate=True, precision="fp32", ell_max=4, P0=0.0, nbar=0.0,
                  max_group_bytes=0, max_kbins=512, max_particles=0, cache_randoms=False, device=None,
-                 stream=None):
+                 stream=None, ylm_table=True):
         import torch
         lib = load()
         self.device = torch.device(device if device is not None else "cuda", )
@@ -166,7 +170,8 @@ class Estimator:
         self.params = Params(int(nmesh), WINDOWS[window], int(bool(interlaced)), int(bool(compensate)),
                              PRECISIONS[precision], int(ell_max), float(box_size),
                              (C.c_double * 3)(*box_corner), (C.c_double * 3)(*observer), float(P0), float(nbar),
-                             int(max_group_bytes), int(max_particles), int(bool(cache_randoms)), 0)
+                             int(max_group_bytes), int(max_particles), int(bool(cache_randoms)),
+                             0 if ylm_table else -1)
         self.max_kbins = int(max_kbins)
         nbytes = C.c_int64(0)
         with torch.cuda.device(self.device):
@@ -218,6 +223,37 @@ class Estimator:
         _check(lib.pspec_multipoles_device(self._ctx, el, len(ells), edges.ctypes.data_as(C.POINTER(C.c_double)),
                                            len(edges) - 1, C.c_void_p(_ptr(P_out)), C.c_void_p(_ptr(kmean_out)),
                                            C.c_void_p(_ptr(nmodes_out))), self._ctx)
+
+    def multipoles_range(self, ells: Sequence[int], k_edges, q0: int, q1: int, include_p0=True, bins=None):
+        """Raw FP64 bin sums, shape (1 + n_ells, nk), of items [q0, q1) of the flat harmonic list
+        (l >= 2 in the order of ells, m = 0, +1, -1, +2, ... within l). Enqueued, not synchronised."""
+        import torch
+        lib = load()
+        ells = [int(e) for e in ells]
+        edges = np.ascontiguousarray(k_edges, dtype=np.float64)
+        nk = len(edges) - 1
+        if bins is None:
+            bins = torch.empty((1 + len(ells), nk), dtype=torch.float64, device=self.device)
+        el = (C.c_int32 * len(ells))(*ells)
+        _check(lib.pspec_multipoles_range(self._ctx, el, len(ells), edges.ctypes.data_as(C.POINTER(C.c_double)), nk,
+                                          int(q0), int(q1), int(bool(include_p0)), C.c_void_p(_ptr(bins))), self._ctx)
+        return bins
+
+    def finalize_bins(self, bins, ells: Sequence[int], k_edges) -> dict:
+        """Multipoles from summed raw bins (device tensors out, enqueued on the context stream)."""
+        import torch
+        lib = load()
+        ells = [int(e) for e in ells]
+        edges = np.ascontiguousarray(k_edges, dtype=np.float64)
+        nk = len(edges) - 1
+        P = torch.empty((len(ells), nk), dtype=torch.float64, device=self.device)
+        km = torch.empty(nk, dtype=torch.float64, device=self.device)
+        nm = torch.empty(nk, dtype=torch.float64, device=self.device)
+        el = (C.c_int32 * len(ells))(*ells)
+        _check(lib.pspec_finalize_bins(self._ctx, C.c_void_p(_ptr(bins)), el, len(ells),
+                                       edges.ctypes.data_as(C.POINTER(C.c_double)), nk, C.c_void_p(_ptr(P)),
+                                       C.c_void_p(_ptr(km)), C.c_void_p(_ptr(nm))), self._ctx)
+        return {"P": P, "k_mean": km, "n_modes": nm, "ells": ells}
 
     # ------------------------------------------------------------------ batched mocks
     def set_randoms(self, pos, weight=None, nbar=None):

@@ -296,3 +296,29 @@ def test_autotune_picks_valid_knobs_and_caches(tmp_path):
     est.close()
     o = E.multipoles(d, r, p, ells, edges)
     check_fp32(g, o, ells, scale=np.abs(o["P"][0]) + o["S"] / o["I"])
+
+
+def test_ylm_table_and_per_mode_paths_match_oracle():
+    """FP32 binning with the Y_lm(khat) table (default) and with per-mode FP32 evaluation
+    (ylm_table = -1) both meet the tolerance; the plan reports the table it holds."""
+    geo = synth.survey_geometry()
+    fld = synth.lognormal_field(64, geo.box_size, geo.box_corner, seed=5)
+    d = synth.survey_catalog(fld, geo, nbar=1e-4, seed=35)
+    r = synth.survey_randoms(5 * d.size, geo, seed=6)
+    p = E.Params(nmesh=64, box_size=geo.box_size, box_corner=tuple(geo.box_corner), window="cic",
+                 interlaced=True, compensate=True, P0=1e4, nbar=1e-4)
+    edges = uniform_edges(0.005, 0.095, 0.01)
+    ells = [0, 2, 4, 6]
+    o = E.multipoles(d, r, p, ells, edges)
+    out = {}
+    for table in (True, False):
+        g = run_gpu(p, d, r, ells, edges, precision="fp32", ylm_table=table)
+        check_fp32(g, o, ells)
+        nbytes = 64 * 64 * 32 * 4 * (5 + 9 + 13)
+        assert g["plan"]["ylm_table_bytes"] == (nbytes if table else 0)
+        out[table] = g["P"]
+    scale = np.abs(o["P"][0])
+    assert np.all(np.abs(out[True] - out[False]) <= 2e-5 * scale[None, :])
+    # FP64 contexts never hold the table
+    g = run_gpu(p, d, r, [0, 2], edges, precision="fp64", ell_max=6)
+    assert g["plan"]["ylm_table_bytes"] == 0
