@@ -547,12 +547,16 @@ def main():
         side["ell_max_16_fp32"] = {"value": ws * max(3, args.steps // 4) / (ms16 / 1000.0), "unit": "sets/s",
                                    "ms_per_set": ms16 / max(3, args.steps // 4)}
         e16.close()
+        del e16
+        torch.cuda.empty_cache()
         # ---- plain FP64 path, l = 0, 2, 4
         e64 = est_for("fp64", 4)
         ms64, _, _, _ = timed(e64, ELLS, max(3, args.steps // 4), 3)
         side["fp64_plain_ell_max_4"] = {"value": ws * max(3, args.steps // 4) / (ms64 / 1000.0), "unit": "sets/s",
                                         "ms_per_set": ms64 / max(3, args.steps // 4)}
         e64.close()
+        del e64
+        torch.cuda.empty_cache()
 
     if not args.quick and nmesh == NMESH:
         side["fp32_batched_ell_max_4"] = batched_measurement(est_for, data, randoms, edges, dev, stream)

@@ -336,9 +336,12 @@ class Estimator:
         return {K_NAMES[k]: {"launches": la[k], "ms": ms[k], "bytes": by[k]} for k in range(n)}
 
     def close(self):
+        """Destroy the context and release its workspace (and the inputs it kept alive)."""
         if getattr(self, "_ctx", None):
             load().pspec_destroy(self._ctx)
             self._ctx = None
+        self._ws = None
+        self._keep = []
 
     def __del__(self):
         try:

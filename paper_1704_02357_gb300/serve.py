@@ -71,6 +71,7 @@ class Server:
         self.max_particles = int(max_particles)
         self.max_group_bytes_for = max_group_bytes_for or (lambda n, l: 0)
         self.max_slots_per_shape = max_slots_per_shape
+        self.headroom = 1 << 30  # device bytes left free beside a new workspace
         self.device = device
         self.clock = clock
         self.slots: List[_Slot] = []
@@ -96,17 +97,29 @@ class Server:
             P._check(lib.pspec_workspace_size(C.byref(p), int(self.kw["max_kbins"]), C.byref(n)))
         return int(n.value) + 256
 
+    def _free_device_bytes(self) -> int:
+        import torch
+        free, _ = torch.cuda.mem_get_info(self.device)
+        return int(free)
+
     def _new_slot(self, key) -> Optional[_Slot]:
         import torch
         nmesh, ell_max = key
         need = self._footprint(nmesh, ell_max)
-        while self.used() + need > self.budget:
+        if need > self.budget:
+            raise ValueError(f"a ({nmesh}^3, l_max {ell_max}) context needs {need} bytes, over the HBM budget")
+        # the budget bounds what this server holds; the device must also have the room now
+        while self.used() + need > self.budget or need + self.headroom > self._free_device_bytes():
             idle = [s for s in self.slots if s.busy is None]
             if not idle:
-                return None
+                if not any(s.busy is not None for s in self.slots):
+                    raise MemoryError(f"a ({nmesh}^3, l_max {ell_max}) context needs {need} bytes; "
+                                      f"the device has {self._free_device_bytes()} free and nothing to evict")
+                return None  # wait for a running request to finish
             victim = min(idle, key=lambda s: s.last_used)
             victim.est.close()
             self.slots.remove(victim)
+            torch.cuda.empty_cache()
         stream = torch.cuda.Stream(device=self.device)
         est = Estimator(nmesh=nmesh, ell_max=ell_max, cache_randoms=True, max_particles=self.max_particles,
                         max_group_bytes=self.max_group_bytes_for(nmesh, ell_max), device=self.device, stream=stream,
@@ -187,9 +200,11 @@ class Server:
         return self.done
 
     def close(self) -> None:
+        import torch
         for s in self.slots:
             s.est.close()
         self.slots.clear()
+        torch.cuda.empty_cache()
 
 
 def latency_summary(done: Sequence[Request], wall: float) -> Dict[str, float]:
