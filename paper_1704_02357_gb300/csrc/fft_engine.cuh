@@ -138,23 +138,33 @@ __device__ __forceinline__ void stage_ct(C (&v)[E], C* sm, int t, int seq, const
   }
 }
 
+// Barrier between exchange steps: the whole block, or (WARP) only the warp, when every
+// sequence's threads lie in one warp and its shared rows are its own.
+template <bool WARP> __device__ __forceinline__ void fft_sync() {
+  if constexpr (WARP)
+    __syncwarp();
+  else
+    __syncthreads();
+}
+
 // Transforms the length-L sequence whose slots this thread holds (DIR = -1 forward, +1
-// inverse). All threads of the block must call it (it contains __syncthreads); the shared
-// buffer is free again when it returns. NSEQ is the number of interleaved sequences
+// inverse). All threads of the block (WARP: of the warp) must call it; the shared buffer of
+// the sequence is free again when it returns. NSEQ is the number of interleaved sequences
 // (kInterleaved only).
-template <typename C, int E, int L, int LAYOUT, int NSEQ, int DIR>
+template <typename C, int E, int L, int LAYOUT, int NSEQ, int DIR, bool WARP = false>
 __device__ __forceinline__ void fft_ct(C (&v)[E], C* sm, int t, int seq, const ux_of<C>* __restrict__ tw) {
   constexpr CtPlan P = ct_plan(L);
   constexpr int Tc = L / E;
+  static_assert(!WARP || (LAYOUT == kPaddedRows && Tc <= 32 && 32 % Tc == 0), "warp-synchronous rows only");
   static_for<0, P.nst>([&](auto s_) {
     constexpr int s = decltype(s_)::value;
     constexpr bool last = (s == P.nst - 1);
     stage_ct<C, E, L, P.rad[s], P.ns[s], last, LAYOUT, NSEQ, DIR>(v, sm, t, seq, tw);
     if constexpr (!last) {
-      __syncthreads();
+      fft_sync<WARP>();
 #pragma unroll
       for (int e = 0; e < E; e++) v[e] = sm[sidx<LAYOUT, L, NSEQ>(seq, t + Tc * e)];
-      __syncthreads();
+      fft_sync<WARP>();
     }
   });
 }

@@ -26,6 +26,7 @@ template <int N> struct Shape {
   static constexpr int NH = N / 2;
   static constexpr int E = elems_for(N);
   static constexpr int Tz = NH / E;      // threads per row in the z passes
+  static constexpr bool ZW = Tz <= 32;   // a z row within one warp: warp-level barriers suffice
   static constexpr int Tc = N / E;       // threads per column in the y / x passes
   static constexpr int TW = col_tile(N); // kz columns per tile
   static constexpr int ROWS = z_rows(N); // rows per block in the plain z passes
@@ -69,10 +70,10 @@ __global__ void __launch_bounds__(Shape<N>::ZT, min_blocks<T, Shape<N>::E>(Shape
   C v[E];
 #pragma unroll
   for (int e = 0; e < E; e++) v[e] = src[t + Tc * e];
-  fft_ct<C, E, L, kPaddedRows, 1, -1>(v, sm, t, r, twh);
+  fft_ct<C, E, L, kPaddedRows, 1, -1, S::ZW>(v, sm, t, r, twh);
 #pragma unroll
   for (int e = 0; e < E; e++) sm[sidx<kPaddedRows, L, 1>(r, t + Tc * e)] = v[e];
-  __syncthreads();
+  fft_sync<S::ZW>();
   C* dst = out + (int64_t)row * L;
 #pragma unroll
   for (int e = 0; e < E; e++) {
@@ -106,7 +107,7 @@ __global__ void __launch_bounds__(Shape<N>::ZT, min_blocks<T, Shape<N>::E>(Shape
     const C od = umul(cscale(csub(xk, xm), T(0.5)), uconj(ldg_u(twr + k)));
     v[e] = mk(ev.x - od.y, ev.y + od.x);  // E + i O
   }
-  fft_ct<C, E, L, kPaddedRows, 1, +1>(v, sm, t, r, twh);
+  fft_ct<C, E, L, kPaddedRows, 1, +1, S::ZW>(v, sm, t, r, twh);
   C* dst = reinterpret_cast<C*>(out + (int64_t)row * N);
 #pragma unroll
   for (int e = 0; e < E; e++) dst[t + Tc * e] = cscale(v[e], scale);
@@ -176,10 +177,10 @@ __global__ void __launch_bounds__(512) k_ylm_r2c_z(const T* __restrict__ f, cx<T
 #pragma unroll
   for (int e = 0; e < E; e++) v[e] = stc[sq * L + t + Tc * e];
   __syncthreads();
-  fft_ct<C, E, L, kPaddedRows, 1, -1>(v, xb, t, sq, twh);
+  fft_ct<C, E, L, kPaddedRows, 1, -1, S::ZW>(v, xb, t, sq, twh);
 #pragma unroll
   for (int e = 0; e < E; e++) xb[sidx<kPaddedRows, L, 1>(sq, t + Tc * e)] = v[e];
-  __syncthreads();
+  fft_sync<S::ZW>();
   const int s = sq / rows, r = sq - s * rows;
   C* dst = out + s * spec_stride + (int64_t)(row0 + r) * L;
 #pragma unroll
