@@ -403,6 +403,116 @@ __global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T, Shape<N>::E>(Shape
   for (int b = threadIdx.x; b < ba.nk; b += blockDim.x) atomicAdd(&ba.bins[slot * ba.nk + b], wb.b[b]);
 }
 
+// ------------------------------------------------------------------ pass x + bin, pipelined (FP32, Y table)
+// Asynchronous global -> shared copies (cp.async): 16 bytes each, tracked per thread in
+// commit groups; a group's data is visible to the block after wait + __syncthreads.
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int NPEND> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory");
+}
+
+// The binning pass of the FP32 path with the Y_lm(khat) table. While harmonic s is
+// transformed, the G tile and the Y tile of harmonic s+1 are copied asynchronously into the
+// other half of a double buffer, so the x pass no longer waits on global loads; the landed G
+// tile also serves as the transform's exchange buffer, and F0 stays in registers (each thread
+// owns its modes for the whole tile).
+template <int N>
+__global__ void __launch_bounds__(Shape<N>::CT, min_blocks<float, Shape<N>::E>(Shape<N>::CT))
+    k_bin_x_pipe(const float2* G, int64_t spec_stride, int ell, int h0, int M, const float2* __restrict__ F0,
+                 const float4* __restrict__ twf, int slot, BinArgs ba, const float* __restrict__ ytab) {
+  using C = float2;
+  using S = Shape<N>;
+  constexpr int NH = S::NH, E = S::E, Tc = S::Tc, TW = S::TW, CT = S::CT;
+  static_assert(TW >= 4, "a tile row must hold whole 16-byte chunks");
+  constexpr int GCH = TW * 8 / 16, YCH = TW * 4 / 16;  // 16-byte chunks per tile row
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sG = reinterpret_cast<C*>(smraw);                  // [2][N * TW]
+  float* sY = reinterpret_cast<float*>(sG + 2 * N * TW);  // [2][N * TW]
+  WarpBins<float> wb;
+  wb.nk = ba.nk;
+  wb.nwarps = (CT + 31) >> 5;
+  wb.b = reinterpret_cast<double*>(sY + 2 * N * TW);
+  wb.w = reinterpret_cast<float*>(wb.b + ba.nk);
+  wb.init();
+  const int c = threadIdx.x % TW, t = threadIdx.x / TW;
+  constexpr int ntz = NH / TW, ntiles = N * ntz;
+  constexpr int64_t si = (int64_t)N * NH;
+  const float* yl = ytab + (int64_t)(ytab_base(ell) + h0) * (si * N);
+  __syncthreads();
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int j = tile / ntz, kz0 = (tile - j * ntz) * TW;
+    const int kz = kz0 + c;
+    const int64_t off0 = (int64_t)j * NH + kz0, off = off0 + c;
+    auto issue = [&](int s, int buf) {
+      const C* Gs = G + (int64_t)s * spec_stride + off0;
+      C* dG = sG + buf * N * TW;
+      for (int q = threadIdx.x; q < N * GCH; q += CT) {
+        const int i = q / GCH, part = q - i * GCH;
+        cp_async16(dG + i * TW + part * 2, Gs + i * si + part * 2);
+      }
+      const float* Ys = yl + (int64_t)s * (si * N) + off0;
+      float* dY = sY + buf * N * TW;
+      for (int q = threadIdx.x; q < N * YCH; q += CT) {
+        const int i = q / YCH, part = q - i * YCH;
+        cp_async16(dY + i * TW + part * 4, Ys + i * si + part * 4);
+      }
+      cp_async_commit();
+    };
+    issue(0, 0);
+    C f0[E];
+    float acc[E];
+#pragma unroll
+    for (int e = 0; e < E; e++) {
+      f0[e] = F0[off + (t + Tc * e) * si];
+      acc[e] = 0.f;
+    }
+    for (int s = 0; s < M; s++) {
+      const int buf = s & 1;
+      if (s + 1 < M) {
+        issue(s + 1, buf ^ 1);  // the other half was last read before the previous transform's final barrier
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncthreads();  // harmonic s landed for the whole block
+      C* tg = sG + buf * N * TW;
+      const float* ty = sY + buf * N * TW;
+      C v[E];
+      float yv[E];
+#pragma unroll
+      for (int e = 0; e < E; e++) {
+        v[e] = tg[(t + Tc * e) * TW + c];
+        yv[e] = ty[(t + Tc * e) * TW + c];
+      }
+      __syncthreads();  // the tile becomes the transform's exchange buffer
+      fft_ct<C, E, N, kInterleaved, TW, -1>(v, tg, t, c, twf);
+#pragma unroll
+      for (int e = 0; e < E; e++) acc[e] += yv[e] * (v[e].x * f0[e].x + v[e].y * f0[e].y);  // Y(k=0) = 0
+    }
+    if (j != N / 2) {
+      const float mult = kz ? 2.f : 1.f;
+      const int ny = sfreq<N>(j);
+#pragma unroll
+      for (int e = 0; e < E; e++) {
+        const int ii = t + Tc * e;
+        if (ii == N / 2) continue;
+        const int nx = sfreq<N>(ii);
+        const int n2 = nx * nx + ny * ny + kz * kz;
+        const int b = ba.bin_of_n2[n2];
+        if (b >= 0 && n2 > 0) wb.add(b, mult * acc[e]);
+      }
+    }
+    __syncthreads();
+    wb.fold();
+    __syncthreads();
+  }
+  for (int b = threadIdx.x; b < ba.nk; b += blockDim.x) atomicAdd(&ba.bins[slot * ba.nk + b], wb.b[b]);
+}
+
 // ------------------------------------------------------------------ launchers of one size
 template <typename K> static void set_smem(K kernel, size_t bytes) {
   if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -416,6 +526,11 @@ template <typename T, int N> struct Passes {
   static size_t smem_bins(int nk) { return (size_t)nk * sizeof(double) + (size_t)((S::CT + 31) / 32) * nk * sizeof(T); }
   static size_t smem_combine(int nk) { return smem_col() + smem_bins(nk); }
   static size_t smem_bin(int nk) { return 2 * smem_col() + smem_bins(nk); }
+  // pipelined FP32 pass: two G tiles and two Y tiles (float), then the bins
+  static size_t smem_bin_pipe(int nk) {
+    return 2 * (size_t)N * S::TW * (sizeof(float2) + sizeof(float)) + (size_t)nk * sizeof(double) +
+           (size_t)((S::CT + 31) / 32) * nk * sizeof(float);
+  }
 
   static void r2c_z(const T* in, C* out, const U* twh, const U* twr, cudaStream_t s) {
     const size_t smem = (size_t)S::ROWS * padded_len(S::NH) * sizeof(C);
@@ -478,6 +593,14 @@ template <typename T, int N> struct Passes {
   static void bin_x(const C* G, int64_t stride, int ell, int h0, int M, const C* F0, const U* twf, int slot,
                     const BinArgs& ba, int ctas, const float* ytab, cudaStream_t s) {
     const size_t smem = smem_bin(ba.nk);
+    if constexpr (sizeof(T) == 4 && S::E == 8) {
+      if (ytab) {
+        const size_t sp = smem_bin_pipe(ba.nk);
+        set_smem(k_bin_x_pipe<N>, sp);
+        k_bin_x_pipe<N><<<ctas, S::CT, sp, s>>>(G, stride, ell, h0, M, F0, twf, slot, ba, ytab);
+        return;
+      }
+    }
     if (ytab && sizeof(T) == 4) {
       set_smem(k_bin_x<T, N, true>, smem);
       k_bin_x<T, N, true><<<ctas, S::CT, smem, s>>>(G, stride, ell, h0, M, F0, twf, slot, ba, ytab, host_ytab<T>());
@@ -492,6 +615,16 @@ template <typename T, int N> struct Passes {
       const size_t smem = smem_combine(nk);
       set_smem(k_combine_x<T, N>, smem);
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_combine_x<T, N>, S::CT, smem);
+    } else if (which == 2 && sizeof(T) == 4 && S::E == 8) {
+      if constexpr (sizeof(T) == 4 && S::E == 8) {
+        const size_t smem = smem_bin_pipe(nk);
+        set_smem(k_bin_x_pipe<N>, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bin_x_pipe<N>, S::CT, smem);
+      }
+    } else if (which == 2) {
+      const size_t smem = smem_bin(nk);
+      set_smem(k_bin_x<T, N, true>, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bin_x<T, N, true>, S::CT, smem);
     } else {
       const size_t smem = smem_bin(nk);
       set_smem(k_bin_x<T, N, false>, smem);
@@ -519,6 +652,7 @@ template <typename T, int N> struct Passes {
     t.ctas = &ctas;
     t.smem_combine = &smem_combine;
     t.smem_bin = &smem_bin;
+    t.smem_bin_pipe = &smem_bin_pipe;
     return t;
   }
 };

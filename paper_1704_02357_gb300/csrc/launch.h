@@ -138,9 +138,10 @@ template <typename T> struct PassTable {
                     int, cudaStream_t);
   void (*bin_x)(const cx<T>*, int64_t, int, int, int, const cx<T>*, const ux<T>*, int, const BinArgs&, int,
                 const float*, cudaStream_t);  // ..., Y_lm(khat) table or nullptr
-  int (*ctas)(int, int, int);  // (which: 0 combine, 1 bin; nk; SM count) -> persistent blocks
+  int (*ctas)(int, int, int);  // (which: 0 combine, 1 bin, 2 pipelined FP32 bin; nk; SMs) -> persistent blocks
   size_t (*smem_combine)(int);
   size_t (*smem_bin)(int);
+  size_t (*smem_bin_pipe)(int);
 };
 template <typename T, int N> const PassTable<T>* pass_table_n();
 // nullptr when N is not a supported mesh side.

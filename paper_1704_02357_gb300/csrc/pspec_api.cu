@@ -103,9 +103,13 @@ pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl,
   int m_mem = p->max_group_bytes > 0 ? (int)(p->max_group_bytes / (int64_t)pl->Sc) : nharm;
   pl->group_max = p->ell_max == 0 ? 0 : std::max(1, std::min(nharm, m_mem));
 
+  // Y_lm(khat) of every stored mode for the FP32 binning pass (l = 2..l_max)
+  pl->ytab_bytes = (size_t)N * N * NH * sizeof(float) * (size_t)ytab_base(p->ell_max + 2);
+  pl->has_ytab = !f64 && p->ell_max >= 2 && p->ylm_table == 0 && pl->ytab_bytes <= (size_t)PSPEC_YLM_TABLE_AUTO_MAX;
   {
-    const size_t need = f64 ? std::max(pl->td->smem_bin(max_kbins), pl->td->smem_combine(max_kbins))
-                            : std::max(pl->tf->smem_bin(max_kbins), pl->tf->smem_combine(max_kbins));
+    size_t need = f64 ? std::max(pl->td->smem_bin(max_kbins), pl->td->smem_combine(max_kbins))
+                      : std::max(pl->tf->smem_bin(max_kbins), pl->tf->smem_combine(max_kbins));
+    if (pl->has_ytab) need = std::max(need, pl->tf->smem_bin_pipe(max_kbins));
     if (need > kSmemMaxBlock) { *why = "max_kbins too large for this mesh (shared memory)"; return PSPEC_EINVAL; }
   }
   if (f64) {
@@ -113,7 +117,7 @@ pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl,
     pl->ctas_bin = pl->td->ctas(1, max_kbins, nsm);
   } else {
     pl->ctas_comb = pl->tf->ctas(0, max_kbins, nsm);
-    pl->ctas_bin = pl->tf->ctas(1, max_kbins, nsm);
+    pl->ctas_bin = pl->tf->ctas(pl->has_ytab ? 2 : 1, max_kbins, nsm);
   }
   pl->nblk_sum = 2 * nsm;
 
@@ -136,9 +140,6 @@ pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl,
   pl->o_axis = take(3 * (size_t)N * pl->esz);
   pl->o_phase = take(3 * (size_t)N * usz);
   pl->o_invw = take((N + NH) * csz);
-  // Y_lm(khat) of every stored mode for the FP32 binning pass (l = 2..l_max)
-  pl->ytab_bytes = (size_t)N * N * NH * sizeof(float) * (size_t)ytab_base(p->ell_max + 2);
-  pl->has_ytab = !f64 && p->ell_max >= 2 && p->ylm_table == 0 && pl->ytab_bytes <= (size_t)PSPEC_YLM_TABLE_AUTO_MAX;
   pl->o_ytab = pl->has_ytab ? take(pl->ytab_bytes) : 0;
   pl->o_bin = take((pl->n2max + 1) * sizeof(int32_t));
   pl->o_kmag = take((pl->n2max + 1) * sizeof(double));
