@@ -54,6 +54,22 @@ __device__ __forceinline__ C r2c_unpack(C zk, C zm, ux<T> w) {
   return cadd(e, umul(o, w));
 }
 
+// X[L - k] for each output k = t + Tc e this thread holds after a row transform, fetched with
+// shuffles from the thread holding it (lane Tc - t of the row, element E - 1 - e); thread 0
+// holds its own mirrors (k = Tc e -> Tc (E - e), and X[0] for k = 0). Rows within one warp.
+template <typename C, int E, int Tc>
+__device__ __forceinline__ void row_mirrors(const C (&v)[E], C (&zm)[E], int t) {
+  static_assert(Tc <= 32 && (Tc & (Tc - 1)) == 0, "row within a warp");
+  const int src = (Tc - t) & (Tc - 1);
+#pragma unroll
+  for (int e = 0; e < E; e++) {
+    C w;
+    w.x = __shfl_sync(0xffffffffu, v[E - 1 - e].x, src, Tc);
+    w.y = __shfl_sync(0xffffffffu, v[E - 1 - e].y, src, Tc);
+    zm[e] = t ? w : v[(E - e) % E];
+  }
+}
+
 // ------------------------------------------------------------------ pass z: r2c of plain rows
 template <typename T, int N>
 __global__ void __launch_bounds__(Shape<N>::ZT, min_blocks<T, Shape<N>::E>(Shape<N>::ZT))
@@ -71,15 +87,24 @@ __global__ void __launch_bounds__(Shape<N>::ZT, min_blocks<T, Shape<N>::E>(Shape
 #pragma unroll
   for (int e = 0; e < E; e++) v[e] = src[t + Tc * e];
   fft_ct<C, E, L, kPaddedRows, 1, -1, S::ZW>(v, sm, t, r, twh);
+  C zm[E];
+  if constexpr (S::ZW) {
+    row_mirrors<C, E, Tc>(v, zm, t);
+  } else {
 #pragma unroll
-  for (int e = 0; e < E; e++) sm[sidx<kPaddedRows, L, 1>(r, t + Tc * e)] = v[e];
-  fft_sync<S::ZW>();
+    for (int e = 0; e < E; e++) sm[sidx<kPaddedRows, L, 1>(r, t + Tc * e)] = v[e];
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < E; e++) {
+      const int k = t + Tc * e;
+      zm[e] = sm[sidx<kPaddedRows, L, 1>(r, k ? L - k : 0)];
+    }
+  }
   C* dst = out + (int64_t)row * L;
 #pragma unroll
   for (int e = 0; e < E; e++) {
     const int k = t + Tc * e;
-    const C zm = sm[sidx<kPaddedRows, L, 1>(r, k ? L - k : 0)];
-    dst[k] = r2c_unpack<C, T>(v[e], zm, ldg_u(twr + k));
+    dst[k] = r2c_unpack<C, T>(v[e], zm[e], ldg_u(twr + k));
   }
 }
 
@@ -119,7 +144,7 @@ __global__ void __launch_bounds__(Shape<N>::ZT, min_blocks<T, Shape<N>::E>(Shape
 // area of nseq = M*rows real rows; then each of the nseq*Tz threads loads its slots, the
 // sequences are transformed (the staging area is reused as the exchange buffer) and
 // unpacked into the M spectra.
-template <typename T, int N>
+template <typename T, int N, int LT>
 __global__ void __launch_bounds__(512) k_ylm_r2c_z(const T* __restrict__ f, cx<T>* __restrict__ out,
                                                   int64_t spec_stride, int ell, int h0, int M,
                                                   const ux<T>* __restrict__ twh, const ux<T>* __restrict__ twr,
@@ -150,23 +175,43 @@ __global__ void __launch_bounds__(512) k_ylm_r2c_z(const T* __restrict__ f, cx<T
       const T inv = rsqrt_fast<T>(r2);
       const T x = vx * inv, y = vy * inv, z = vz * inv;
       T pr = T(1), pi = T(0);
-      for (int s = 0; s < a_lo; s++) {
-        const T nr = pr * x - pi * y;
-        pi = pr * y + pi * x;
-        pr = nr;
-      }
-      for (int a = a_lo; a <= a_hi; a++) {
-        const T q = fv * ylm_q<T, false>(yt, ell, a, z);
-        if (a == 0) {
-          stage[r * N + kk] = q;
-        } else {
-          const int hp = 2 * a - 1, hm = 2 * a;
-          if (hp >= h0 && hp < h0 + M) stage[((hp - h0) * rows + r) * N + kk] = sq2 * q * pr;
-          if (hm >= h0 && hm < h0 + M) stage[((hm - h0) * rows + r) * N + kk] = sq2 * q * pi;
+      if constexpr (LT > 0) {
+        // l known at compile time: every recurrence unrolled with constant coefficient offsets
+#pragma unroll
+        for (int a = 0; a <= LT; a++) {
+          if (a >= a_lo && a <= a_hi) {
+            const T q = fv * ylm_q<T, false>(yt, LT, a, z);
+            if (a == 0) {
+              stage[r * N + kk] = q;
+            } else {
+              const int hp = 2 * a - 1, hm = 2 * a;
+              if (hp >= h0 && hp < h0 + M) stage[((hp - h0) * rows + r) * N + kk] = sq2 * q * pr;
+              if (hm >= h0 && hm < h0 + M) stage[((hm - h0) * rows + r) * N + kk] = sq2 * q * pi;
+            }
+          }
+          const T nr = pr * x - pi * y;
+          pi = pr * y + pi * x;
+          pr = nr;
         }
-        const T nr = pr * x - pi * y;
-        pi = pr * y + pi * x;
-        pr = nr;
+      } else {
+        for (int s = 0; s < a_lo; s++) {
+          const T nr = pr * x - pi * y;
+          pi = pr * y + pi * x;
+          pr = nr;
+        }
+        for (int a = a_lo; a <= a_hi; a++) {
+          const T q = fv * ylm_q<T, false>(yt, ell, a, z);
+          if (a == 0) {
+            stage[r * N + kk] = q;
+          } else {
+            const int hp = 2 * a - 1, hm = 2 * a;
+            if (hp >= h0 && hp < h0 + M) stage[((hp - h0) * rows + r) * N + kk] = sq2 * q * pr;
+            if (hm >= h0 && hm < h0 + M) stage[((hm - h0) * rows + r) * N + kk] = sq2 * q * pi;
+          }
+          const T nr = pr * x - pi * y;
+          pi = pr * y + pi * x;
+          pr = nr;
+        }
       }
     }
   }
@@ -178,6 +223,7 @@ __global__ void __launch_bounds__(512) k_ylm_r2c_z(const T* __restrict__ f, cx<T
   for (int e = 0; e < E; e++) v[e] = stc[sq * L + t + Tc * e];
   __syncthreads();
   fft_ct<C, E, L, kPaddedRows, 1, -1, S::ZW>(v, xb, t, sq, twh);
+  // mirrors through shared memory (shuffles would raise this kernel's register count, measured slower)
 #pragma unroll
   for (int e = 0; e < E; e++) xb[sidx<kPaddedRows, L, 1>(sq, t + Tc * e)] = v[e];
   fft_sync<S::ZW>();
@@ -550,9 +596,20 @@ template <typename T, int N> struct Passes {
   static void ylm_z(const T* f, C* out, int64_t stride, int ell, int h0, int M, const U* twh, const U* twr,
                     const T* axis, int rows, cudaStream_t s) {
     const size_t smem = smem_ylm(M, rows);
-    set_smem(k_ylm_r2c_z<T, N>, smem);
-    k_ylm_r2c_z<T, N><<<N * N / rows, M * rows * S::Tz, smem, s>>>(f, out, stride, ell, h0, M, twh, twr, axis, rows,
-                                                                    host_ytab<T>());
+    const dim3 grid(N * N / rows), block(M * rows * S::Tz);
+    switch (ell) {  // the headline multipoles get unrolled recurrences
+      case 2:
+        set_smem(k_ylm_r2c_z<T, N, 2>, smem);
+        k_ylm_r2c_z<T, N, 2><<<grid, block, smem, s>>>(f, out, stride, ell, h0, M, twh, twr, axis, rows, host_ytab<T>());
+        break;
+      case 4:
+        set_smem(k_ylm_r2c_z<T, N, 4>, smem);
+        k_ylm_r2c_z<T, N, 4><<<grid, block, smem, s>>>(f, out, stride, ell, h0, M, twh, twr, axis, rows, host_ytab<T>());
+        break;
+      default:
+        set_smem(k_ylm_r2c_z<T, N, 0>, smem);
+        k_ylm_r2c_z<T, N, 0><<<grid, block, smem, s>>>(f, out, stride, ell, h0, M, twh, twr, axis, rows, host_ytab<T>());
+    }
   }
   // variant 0: TW columns per block; variant 1: TW/2 (half the threads and shared memory)
   template <int TWV> static void fft_y_tw(C* data, int64_t stride, int nspec, const U* twf, int dir, cudaStream_t s) {
