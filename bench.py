@@ -434,8 +434,8 @@ def main():
     corner = tuple(geo.box_corner)
     stream = torch.cuda.current_stream(dev)
 
-    def est_for(precision, ell_max):
-        return Estimator(nmesh=nmesh, box_size=BOX, box_corner=corner, observer=(0.0, 0.0, 0.0), window="cic",
+    def est_for(precision, ell_max, window="cic"):
+        return Estimator(nmesh=nmesh, box_size=BOX, box_corner=corner, observer=(0.0, 0.0, 0.0), window=window,
                          interlaced=True, compensate=True, precision=precision, ell_max=ell_max, P0=P0, nbar=NBAR,
                          max_kbins=nk, max_particles=int(data.size + randoms.size), device=dev, stream=stream)
 
@@ -511,6 +511,27 @@ def main():
                   for k, v in kt.items() if v["launches"]}
     total_bytes = info["model_bytes_last"]
 
+    # ---- comparison only: cuFFT (torch.fft.rfftn) on one FP32 mesh vs this library's forward
+    # 3-D r2c (z pass + y pass per spectrum + plain x pass, from the timed region's per-launch times)
+    cufft = None
+    if nmesh == NMESH and kt["r2c_z"]["launches"] and kt["fft_x"]["launches"] and kt["fft_y"]["launches"]:
+        mesh = torch.randn((nmesh,) * 3, device=dev, dtype=torch.float32)
+        for _ in range(3):
+            torch.fft.rfftn(mesh)
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(10):
+            torch.fft.rfftn(mesh)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        sc = nmesh * nmesh * (nmesh // 2) * 8.0  # one stored half spectrum (bytes)
+        y_per = kt["fft_y"]["ms"] * (2 * sc) / kt["fft_y"]["bytes"] if kt["fft_y"]["bytes"] else None
+        ours = (kt["r2c_z"]["ms"] / kt["r2c_z"]["launches"] + (y_per or 0.0) + kt["fft_x"]["ms"] / kt["fft_x"]["launches"])
+        cufft = {"torch_rfftn_ms": c0.elapsed_time(c1) / 10, "ours_r2c_3pass_ms": ours,
+                 "note": "512^3 FP32 real -> half spectrum; comparison only (cuFFT is not on the path)"}
+        del mesh
+
     # ---- e2e: host-resident catalogs (pinned), copied in every step; results read back
     dh = torch.as_tensor(data.pos).pin_memory()
     rh = torch.as_tensor(randoms.pos).pin_memory()
@@ -541,11 +562,12 @@ def main():
 
     side = {}
     if not args.quick:
-        # ---- l <= 16 (153 transforms by the paper's count), FP32
-        e16 = est_for("fp32", 16)
+        # ---- l <= 16 (153 transforms by the paper's count), FP32, TSC + interlacing
+        e16 = est_for("fp32", 16, window="tsc")
         ms16, _, _, _ = timed(e16, ELLS16, max(3, args.steps // 4), 3)
         side["ell_max_16_fp32"] = {"value": ws * max(3, args.steps // 4) / (ms16 / 1000.0), "unit": "sets/s",
-                                   "ms_per_set": ms16 / max(3, args.steps // 4)}
+                                   "ms_per_set": ms16 / max(3, args.steps // 4), "window": "tsc",
+                                   "ylm_table_bytes": e16.plan_info()["ylm_table_bytes"]}
         e16.close()
         del e16
         torch.cuda.empty_cache()
@@ -590,6 +612,7 @@ def main():
                               "achieved_GBps": total_bytes / 1e9 / (ms_step / 1e3),
                               "frac": total_bytes / 1e9 / (ms_step / 1e3) / peak},
             "kernels": per_kernel,
+            "cufft_comparison": cufft,
             "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clocks,
