@@ -434,10 +434,10 @@ def main():
     corner = tuple(geo.box_corner)
     stream = torch.cuda.current_stream(dev)
 
-    def est_for(precision, ell_max, window="cic"):
+    def est_for(precision, ell_max, window="cic", **kw):
         return Estimator(nmesh=nmesh, box_size=BOX, box_corner=corner, observer=(0.0, 0.0, 0.0), window=window,
                          interlaced=True, compensate=True, precision=precision, ell_max=ell_max, P0=P0, nbar=NBAR,
-                         max_kbins=nk, max_particles=int(data.size + randoms.size), device=dev, stream=stream)
+                         max_kbins=nk, max_particles=int(data.size + randoms.size), device=dev, stream=stream, **kw)
 
     dpos = torch.as_tensor(data.pos, device=dev)
     rpos = torch.as_tensor(randoms.pos, device=dev)
@@ -578,6 +578,38 @@ def main():
                                         "ms_per_set": ms64 / max(3, args.steps // 4)}
         e64.close()
         del e64
+        torch.cuda.empty_cache()
+        # ---- the paper's comparison: spherical-harmonic route (1+5+9 transforms) against the
+        # Cartesian decomposition (1+6+15), same context, catalog and kernels, l = 0,2,4
+        ec = est_for("fp32", 4, cartesian=True)
+        reps = max(3, args.steps // 4)
+
+        def route_ms(fn):
+            for _ in range(2):
+                ec.paint(dpos, rpos, stats=False)
+                fn(ELLS, edges)
+            barrier()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for _ in range(reps):
+                ec.paint(dpos, rpos, stats=False)
+                fn(ELLS, edges)
+            a1.record(stream)
+            barrier()
+            return a0.elapsed_time(a1) / reps
+
+        t_sh = route_ms(ec.multipoles)
+        n_sh = ec.plan_info()["transforms_executed"]
+        t_ca = route_ms(ec.multipoles_cartesian)
+        n_ca = ec.plan_info()["transforms_executed"]
+        side["sh_vs_cartesian_ell_max_4_fp32"] = {
+            "sh_ms_per_set": t_sh, "cartesian_ms_per_set": t_ca, "time_ratio_cartesian_over_sh": t_ca / t_sh,
+            "transforms_executed": {"sh": n_sh, "cartesian": n_ca},
+            "paper_transform_count": {"sh": 15, "cartesian": 22},
+            "note": "same context, catalog and kernels; host-synchronised calls (pspec_multipoles vs pspec_multipoles_cartesian)"}
+        ec.close()
+        del ec
         torch.cuda.empty_cache()
 
     if not args.quick and nmesh == NMESH:

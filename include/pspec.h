@@ -90,6 +90,9 @@ typedef struct {
                               Without the table the binning pass evaluates Y_lm(khat) in FP32;
                               its rounding is biased by a few percent of an ulp over a k shell,
                               which lets ~4e-9 of the shot-noise power into P_l (l >= 2) */
+  int32_t cartesian;       /* 0/1 (FP32 contexts): also hold the k-space factors of the Cartesian
+                              decomposition (21 values per stored mode, FP64-built, 5.6 GB at
+                              512^3) for pspec_multipoles_cartesian */
 } pspec_params;
 #define PSPEC_YLM_TABLE_AUTO_MAX ((int64_t)64 << 30)
 
@@ -165,6 +168,17 @@ pspec_status pspec_finalize_bins(void* ctx, const double* bins, const int32_t* e
                                  const double* k_edges, int32_t n_kbins, double* P_dev, double* k_mean_dev,
                                  double* n_modes_dev);
 
+/* The same multipoles (l in {0, 2, 4}) through the Cartesian decomposition that the paper
+ * compares the spherical-harmonic route against (Sec. 2.1: (khat . rhat)^n expanded into the
+ * monomials khat_i ... rhat_i ...; 1 + 6 + 15 = 22 transforms for l <= 4 against 1 + 5 + 9 = 15).
+ * Transforms of f times each monomial rhat^q of degree 2 and 4 are binned against F0 with the
+ * factors mult_q khat^q; P_2 = 5/2 (3 A_2 - B_0)/(I N_b), P_4 = 9/8 (35 A_4 - 30 A_2 + 3 B_0)/(I N_b),
+ * with B_0 the l = 0 sum before the shot-noise subtraction. Equal to pspec_multipoles in
+ * exact arithmetic. Needs an FP32 context created with cartesian = 1 (else PSPEC_EUNSUPPORTED);
+ * outputs and synchronisation as pspec_multipoles. */
+pspec_status pspec_multipoles_cartesian(void* ctx, const int32_t* ells, int32_t n_ells, const double* k_edges,
+                                        int32_t n_kbins, double* P, double* k_mean, double* n_modes);
+
 /* Batched mocks sharing one randoms catalog (the batching pattern of the mock campaigns
  * that motivate the method, Sec. 1 and Sec. 5). Needs a context created with cache_randoms = 1.
  * pspec_set_randoms paints the randoms once (unscaled) into cached meshes and keeps their
@@ -235,6 +249,7 @@ typedef struct {
   int64_t kernel_launches;                    /* cumulative kernels launched by this context */
   double model_bytes_last;                    /* algorithmic HBM bytes of the last paint+multipoles */
   int64_t ylm_table_bytes;                    /* Y_lm(khat) table held (0: evaluated per mode) */
+  int64_t cartesian_table_bytes;              /* Cartesian k-space factors held (0: none) */
 } pspec_plan_info;
 pspec_status pspec_get_plan_info(void* ctx, pspec_plan_info* info);
 

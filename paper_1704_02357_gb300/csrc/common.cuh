@@ -189,6 +189,41 @@ __device__ __forceinline__ T ylm_q(const YTab<T>& t, int ell, int a, T z) {
   return q1;
 }
 
+// Cartesian decomposition (the route the paper compares against, Sec. 2.1): monomials
+// xhat^a yhat^b zhat^c of degree 2 (q = 0..5) and 4 (q = 6..20), and their multinomial
+// coefficients deg! / (a! b! c!), so that sum_q mult_q khat^q rhat^q = (khat . rhat)^deg.
+constexpr int kCartItems = 21;
+__host__ __device__ __forceinline__ void cart_exp(int q, int& a, int& b, int& c) {
+  if (q < 6) {  // (2,0,0) (0,2,0) (0,0,2) (1,1,0) (1,0,1) (0,1,1)
+    a = q == 0 ? 2 : (q == 3 || q == 4 ? 1 : 0);
+    b = q == 1 ? 2 : (q == 3 || q == 5 ? 1 : 0);
+    c = 2 - a - b;
+    return;
+  }
+  int r = q - 6;  // a from 4 down to 0, then b from 4 - a down to 0
+  for (a = 4; a >= 0; a--) {
+    const int nb = 5 - a;
+    if (r < nb) {
+      b = 4 - a - r;
+      c = 4 - a - b;
+      return;
+    }
+    r -= nb;
+  }
+  a = b = c = 0;
+}
+__host__ __device__ __forceinline__ int cart_mult(int q) {
+  int a, b, c;
+  cart_exp(q, a, b, c);
+  const int f[5] = {1, 1, 2, 6, 24};
+  return f[a + b + c] / (f[a] * f[b] * f[c]);
+}
+template <typename T> __device__ __forceinline__ T ipow(T x, int n) {
+  T r = T(1);
+  for (int i = 0; i < n; i++) r *= x;
+  return r;
+}
+
 // Harmonic index h within multipole l: h = 0 -> m = 0; h = 2a-1 -> m = +a; h = 2a -> m = -a.
 __host__ __device__ __forceinline__ int harm_a(int h) { return (h + 1) >> 1; }
 __host__ __device__ __forceinline__ int harm_sign(int h) { return h == 0 ? 0 : ((h & 1) ? 1 : -1); }

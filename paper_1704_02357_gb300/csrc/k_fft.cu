@@ -140,6 +140,29 @@ void launch_ytab_build(float* ytab, int N, int ell_max, int nsm, cudaStream_t s)
   k_ytab_build<<<8 * nsm, 256, 0, s>>>(ytab, N, ell_max, host_ytab<double>());
 }
 
+// Cartesian k-space factors: ctab[q * modes + (i N + j) NH + kz] = mult_q khat^q in FP64,
+// rounded once to FP32 (0 for k = 0).
+__global__ void __launch_bounds__(256) k_ctab_build(float* __restrict__ ctab, int N) {
+  const int NH = N / 2;
+  const int64_t modes = (int64_t)N * N * NH;
+  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < modes; m += (int64_t)gridDim.x * blockDim.x) {
+    const int kz = (int)(m % NH);
+    const int64_t ij = m / NH;
+    const int j = (int)(ij % N), i = (int)(ij / N);
+    const double fx = i < NH ? i : i - N, fy = j < NH ? j : j - N, fz = kz;
+    const double r2 = fx * fx + fy * fy + fz * fz;
+    const double inv = r2 > 0.0 ? 1.0 / sqrt(r2) : 0.0;
+    const double x = fx * inv, y = fy * inv, z = fz * inv;
+    for (int q = 0; q < kCartItems; q++) {
+      int a, b, c;
+      cart_exp(q, a, b, c);
+      ctab[(int64_t)q * modes + m] = (float)(cart_mult(q) * ipow(x, a) * ipow(y, b) * ipow(z, c));
+    }
+  }
+}
+
+void launch_ctab_build(float* ctab, int N, int nsm, cudaStream_t s) { k_ctab_build<<<8 * nsm, 256, 0, s>>>(ctab, N); }
+
 // ------------------------------------------------------------------ dispatch
 template <typename T> const PassTable<T>* pass_table(int N) {
   switch (N) {

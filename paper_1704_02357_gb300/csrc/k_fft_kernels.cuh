@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(512) k_ylm_r2c_z(const T* __restrict__ f, cx<T
   T* stage = reinterpret_cast<T*>(smraw);  // [nseq][N] reals, then the exchange buffer
   C* xb = reinterpret_cast<C*>(smraw);
   const int row0 = blockIdx.x * rows;
-  const int a_lo = harm_a(h0), a_hi = harm_a(h0 + M - 1);
+  const int a_lo = LT < 0 ? 0 : harm_a(h0), a_hi = LT < 0 ? 0 : harm_a(h0 + M - 1);
   const T sq2 = T(1.41421356237309504880);
   for (int r = 0; r < rows; r++) {
     const int grow = row0 + r;
@@ -170,6 +170,18 @@ __global__ void __launch_bounds__(512) k_ylm_r2c_z(const T* __restrict__ f, cx<T
       const T r2 = vx * vx + vy * vy + vz * vz;
       if (r2 == T(0)) {
         for (int s = 0; s < M; s++) stage[(s * rows + r) * N + kk] = T(0);
+        continue;
+      }
+      if constexpr (LT < 0) {
+        // Cartesian decomposition: weights rhat^q of the monomials h0..h0+M-1 of degree -LT
+        // (refined 1/|r|: the shot noise cancels only in the final combination of degrees)
+        const T inv = rsqrt_t<T>(r2);
+        const T x = vx * inv, y = vy * inv, z = vz * inv;
+        for (int s = 0; s < M; s++) {
+          int ea, eb, ec;
+          cart_exp((LT == -4 ? 6 : 0) + h0 + s, ea, eb, ec);
+          stage[(s * rows + r) * N + kk] = fv * (ipow(x, ea) * ipow(y, eb) * ipow(z, ec));
+        }
         continue;
       }
       const T inv = rsqrt_fast<T>(r2);
@@ -394,7 +406,7 @@ __global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T, Shape<N>::E>(Shape
       const int a = harm_a(h), sg = harm_sign(h);
       const C* Gs = G + (int64_t)s * spec_stride;
       // FP32 with a table: Y_lm(khat) of this harmonic, same mode layout as the spectra
-      const float* Ys = YT ? ytab + (int64_t)(ytab_base(ell) + h) * (si * N) + off : nullptr;
+      const float* Ys = YT ? ytab + (int64_t)s * (si * N) + off : nullptr;
       C v[E];
       float yv[YT ? E : 1];  // table values, loaded with the spectrum so that the FFT hides their latency
 #pragma unroll
@@ -487,7 +499,7 @@ __global__ void __launch_bounds__(Shape<N>::CT, min_blocks<float, Shape<N>::E>(S
   const int c = threadIdx.x % TW, t = threadIdx.x / TW;
   constexpr int ntz = NH / TW, ntiles = N * ntz;
   constexpr int64_t si = (int64_t)N * NH;
-  const float* yl = ytab + (int64_t)(ytab_base(ell) + h0) * (si * N);
+  const float* yl = ytab;  // slot of harmonic h0; the group's slots follow
   __syncthreads();
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int j = tile / ntz, kz0 = (tile - j * ntz) * TW;
@@ -605,6 +617,14 @@ template <typename T, int N> struct Passes {
       case 4:
         set_smem(k_ylm_r2c_z<T, N, 4>, smem);
         k_ylm_r2c_z<T, N, 4><<<grid, block, smem, s>>>(f, out, stride, ell, h0, M, twh, twr, axis, rows, host_ytab<T>());
+        break;
+      case -2:  // Cartesian monomials of degree 2 (h = monomial index)
+        set_smem(k_ylm_r2c_z<T, N, -2>, smem);
+        k_ylm_r2c_z<T, N, -2><<<grid, block, smem, s>>>(f, out, stride, ell, h0, M, twh, twr, axis, rows, host_ytab<T>());
+        break;
+      case -4:
+        set_smem(k_ylm_r2c_z<T, N, -4>, smem);
+        k_ylm_r2c_z<T, N, -4><<<grid, block, smem, s>>>(f, out, stride, ell, h0, M, twh, twr, axis, rows, host_ytab<T>());
         break;
       default:
         set_smem(k_ylm_r2c_z<T, N, 0>, smem);

@@ -682,7 +682,7 @@ struct EllList {
 
 __global__ void k_finalize(const double* __restrict__ bins, const double* __restrict__ nmodes_in,
                            const double* __restrict__ ksum, int nk, EllList el, const double* __restrict__ derived,
-                           double* P, double* kmean, double* nmodes) {
+                           double* P, double* kmean, double* nmodes, int cart) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nk) return;
   const double n = nmodes_in[b];
@@ -693,20 +693,27 @@ __global__ void k_finalize(const double* __restrict__ bins, const double* __rest
   for (int i = 0; i < el.n; i++) {
     const int ell = el.ell[i];
     double v;
+    const double B0 = bins[SLOT_P0 * nk + b];
     if (ell == 0)
-      v = (bins[SLOT_P0 * nk + b] / n - S) / I;
-    else
+      v = (B0 / n - S) / I;
+    else if (!cart)
       v = 4.0 * M_PI * bins[(SLOT_ELL0 + i) * nk + b] / (I * n);
+    else {
+      // Cartesian: A2, A4 = sum mult (khat . rhat)^2, ^4 terms; L_2 = (3mu^2-1)/2, L_4 = (35mu^4-30mu^2+3)/8
+      const double A2 = bins[SLOT_ELL0 * nk + b], A4 = bins[(SLOT_ELL0 + 1) * nk + b];
+      v = ell == 2 ? 2.5 * (3.0 * A2 - B0) / (I * n) : 1.125 * (35.0 * A4 - 30.0 * A2 + 3.0 * B0) / (I * n);
+    }
     P[(int64_t)i * nk + b] = n > 0.0 ? v : nan;
   }
 }
 
 void launch_finalize(const double* bins, const double* nmodes_in, const double* ksum, int nk, const int32_t* ells,
-                     int n_ells, const double* derived, double* P, double* k_mean, double* n_modes, cudaStream_t s) {
+                     int n_ells, const double* derived, double* P, double* k_mean, double* n_modes, cudaStream_t s,
+                     int cartesian) {
   EllList el;
   el.n = n_ells;
   for (int i = 0; i < n_ells; i++) el.ell[i] = ells[i];
-  k_finalize<<<(nk + 127) / 128, 128, 0, s>>>(bins, nmodes_in, ksum, nk, el, derived, P, k_mean, n_modes);
+  k_finalize<<<(nk + 127) / 128, 128, 0, s>>>(bins, nmodes_in, ksum, nk, el, derived, P, k_mean, n_modes, cartesian);
 }
 
 // ------------------------------------------------------------------ a7: wedges

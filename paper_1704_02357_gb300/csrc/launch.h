@@ -125,6 +125,8 @@ __host__ __device__ constexpr int ytab_base(int ell) {
   return b;
 }
 void launch_ytab_build(float* ytab, int N, int ell_max, int nsm, cudaStream_t s);
+// Cartesian k-space factors mult_q khat^q of every stored mode, q = 0..20 (kCartItems slots).
+void launch_ctab_build(float* ctab, int N, int nsm, cudaStream_t s);
 
 template <typename T> struct PassTable {
   int N, E, tw, rows_z, tz;
@@ -137,7 +139,7 @@ template <typename T> struct PassTable {
   void (*combine_x)(const cx<T>*, cx<T>*, const ux<T>*, int, int, int, const ux<T>*, const cx<T>*, const BinArgs&,
                     int, cudaStream_t);
   void (*bin_x)(const cx<T>*, int64_t, int, int, int, const cx<T>*, const ux<T>*, int, const BinArgs&, int,
-                const float*, cudaStream_t);  // ..., Y_lm(khat) table or nullptr
+                const float*, cudaStream_t);  // ..., table slot of the group's first harmonic, or nullptr
   int (*ctas)(int, int, int);  // (which: 0 combine, 1 bin, 2 pipelined FP32 bin; nk; SMs) -> persistent blocks
   size_t (*smem_combine)(int);
   size_t (*smem_bin)(int);
@@ -156,7 +158,8 @@ void launch_bin_counts(const unsigned int* cnt, const double* kmag, const int* l
 
 // a6: bin sums -> P_l, k_mean, n_modes (device doubles).
 void launch_finalize(const double* bins, const double* nmodes, const double* ksum, int nk, const int32_t* ells,
-                     int n_ells, const double* derived, double* P, double* k_mean, double* n_modes, cudaStream_t s);
+                     int n_ells, const double* derived, double* P, double* k_mean, double* n_modes, cudaStream_t s,
+                     int cartesian = 0);
 
 // a7: out[w][b] = sum_i P[i][b] lbar[i][w].
 constexpr int kMaxWedgeTab = 9 * 64;

@@ -52,8 +52,8 @@ struct Plan {
   size_t Sr, Sc;
   int n2max;
   // workspace offsets
-  bool has_ytab = false;
-  size_t ytab_bytes = 0, o_ytab = 0;
+  bool has_ytab = false, has_ctab = false;
+  size_t ytab_bytes = 0, o_ytab = 0, ctab_bytes = 0, o_ctab = 0;
   size_t o_mesh1, o_mesh2, o_f0, o_w, o_f, o_g, o_twh, o_twf, o_twr, o_axis, o_phase, o_invw, o_bin, o_kmag, o_cnt,
       o_lo, o_hi, o_nmodes, o_ksum, o_sums, o_derived, o_bins, o_out, o_tcnt, o_toff, o_tcur, o_prec, o_ptile,
       o_psort, total;
@@ -77,6 +77,8 @@ pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl,
   if (max_kbins < 1 || max_kbins > PSPEC_MAX_KBINS) { *why = "max_kbins out of range"; return PSPEC_EINVAL; }
   if (p->max_group_bytes < 0) { *why = "max_group_bytes < 0"; return PSPEC_EINVAL; }
   if (p->ylm_table != 0 && p->ylm_table != -1) { *why = "ylm_table must be 0 or -1"; return PSPEC_EINVAL; }
+  if (p->cartesian != 0 && p->cartesian != 1) { *why = "cartesian must be 0 or 1"; return PSPEC_EINVAL; }
+  if (p->cartesian && p->precision == PSPEC_FP64) { *why = "the Cartesian route is built for FP32 contexts"; return PSPEC_EUNSUPPORTED; }
   if (p->max_particles < 0 || p->max_particles > (int64_t)0xfffffff0) { *why = "max_particles out of range"; return PSPEC_EINVAL; }
 
   const bool f64 = p->precision == PSPEC_FP64;
@@ -141,6 +143,9 @@ pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl,
   pl->o_phase = take(3 * (size_t)N * usz);
   pl->o_invw = take((N + NH) * csz);
   pl->o_ytab = pl->has_ytab ? take(pl->ytab_bytes) : 0;
+  pl->has_ctab = !f64 && p->cartesian == 1;
+  pl->ctab_bytes = pl->has_ctab ? (size_t)N * N * NH * sizeof(float) * kCartItems : 0;
+  pl->o_ctab = pl->has_ctab ? take(pl->ctab_bytes) : 0;
   pl->o_bin = take((pl->n2max + 1) * sizeof(int32_t));
   pl->o_kmag = take((pl->n2max + 1) * sizeof(double));
   pl->o_cnt = take((pl->n2max + 1) * sizeof(uint32_t));
@@ -314,6 +319,8 @@ pspec_status upload_tables(Ctx* c) {
   TRY(run(c, PSPEC_K_OTHER, 0.0, [&] { launch_mode_counts(pl.g, c->at<uint32_t>(pl.o_cnt), c->nsm, c->stream); }));
   if (pl.has_ytab)
     TRY(run(c, PSPEC_K_OTHER, 0.0, [&] { launch_ytab_build(c->at<float>(pl.o_ytab), N, c->p.ell_max, c->nsm, c->stream); }));
+  if (pl.has_ctab)
+    TRY(run(c, PSPEC_K_OTHER, 0.0, [&] { launch_ctab_build(c->at<float>(pl.o_ctab), N, c->nsm, c->stream); }));
   e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "table upload");
   return PSPEC_OK;
@@ -473,6 +480,7 @@ struct HRange {
   int q1 = 1 << 30;
   bool include_p0 = true;
   double* bins_out = nullptr;  // raw bins instead of finalized multipoles
+  bool cartesian = false;      // Cartesian decomposition (monomials of degree 2 and 4)
 };
 
 template <typename T>
@@ -502,7 +510,7 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
   ba.bin_of_n2 = c->at<int32_t>(pl.o_bin);
   ba.nk = nk;
   ba.bins = c->at<double>(pl.o_bins);
-  cudaError_t e = cudaMemsetAsync(ba.bins, 0, (size_t)(SLOT_ELL0 + n_ells) * nk * sizeof(double), s);
+  cudaError_t e = cudaMemsetAsync(ba.bins, 0, (size_t)(SLOT_ELL0 + std::max(n_ells, 2)) * nk * sizeof(double), s);
   if (e != cudaSuccess) return cuda_fail(c, e, "bins clear");
   int64_t transforms = 0;
   double bytes = 0;
@@ -541,15 +549,39 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
     transforms++;
   }
 
-  // a4 + a5: per multipole l >= 2, groups of harmonics (those of [q0, q1) of the flat list)
+  // a4 + a5: per multipole l >= 2 (or per monomial degree of the Cartesian route), groups of
+  // harmonics (those of [q0, q1) of the flat list)
   int64_t sh = 0;
   const int64_t stride = (int64_t)N * N * g.NH;
+  struct Job {
+    int zarg, nh, slot;
+    const float* table;  // k-space factor slot of item 0, or nullptr
+  };
+  Job jobs[kMaxElls];
+  int njobs = 0;
+  if (!hr.cartesian) {
+    int qbase = 0;
+    for (int i = 0; i < n_ells; i++) {
+      const int ell = ells[i];
+      sh += 2 * ell + 1;
+      if (ell == 0) continue;
+      const int nh = 2 * ell + 1;
+      const float* tb = pl.has_ytab ? c->at<float>(pl.o_ytab) + (int64_t)ytab_base(ell) * stride : nullptr;
+      jobs[njobs++] = {ell, nh, SLOT_ELL0 + i, tb};
+      (void)qbase;
+    }
+  } else {
+    int lmax = 0;
+    for (int i = 0; i < n_ells; i++) lmax = std::max(lmax, (int)ells[i]);
+    sh = 1 + (lmax >= 2 ? 6 : 0) + (lmax >= 4 ? 15 : 0);
+    const float* ct = c->at<float>(pl.o_ctab);
+    if (lmax >= 2) jobs[njobs++] = {-2, 6, SLOT_ELL0, ct};
+    if (lmax >= 4) jobs[njobs++] = {-4, 15, SLOT_ELL0 + 1, ct + 6 * stride};
+  }
   int qbase = 0;
-  for (int i = 0; i < n_ells; i++) {
-    const int ell = ells[i];
-    sh += 2 * ell + 1;
-    if (ell == 0) continue;
-    const int nh = 2 * ell + 1;
+  for (int jb = 0; jb < njobs; jb++) {
+    const int ell = jobs[jb].zarg;
+    const int nh = jobs[jb].nh;
     const int hlo = std::max(0, hr.q0 - qbase), hhi = std::min(nh, hr.q1 - qbase);
     qbase += nh;
     for (int h0 = hlo; h0 < hhi; h0 += pl.group_max) {
@@ -566,10 +598,10 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
         }));
       }
       TRY(run(c, PSPEC_K_FFT_Y, acc(2 * M * Sc), [&] { PT->fft_y(G, stride, M, twf, -1, c->tune.tile_y, s); }));
-      const float* ytab = pl.has_ytab ? c->at<float>(pl.o_ytab) : nullptr;
+      const float* ytab = jobs[jb].table ? jobs[jb].table + (int64_t)h0 * stride : nullptr;
       const double ybytes = ytab ? M * (double)N * N * g.NH * sizeof(float) : 0.0;
       TRY(run(c, PSPEC_K_BIN_X, acc(Sc + M * Sc + ybytes), [&] {
-        PT->bin_x(G, stride, ell, h0, M, F0, twf, SLOT_ELL0 + i, ba, ctas_bin, ytab, s);
+        PT->bin_x(G, stride, ell, h0, M, F0, twf, jobs[jb].slot, ba, ctas_bin, ytab, s);
       }));
       transforms += M;
     }
@@ -587,7 +619,7 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
   // a6
   TRY(run(c, PSPEC_K_FINAL, 0.0, [&] {
     launch_finalize(ba.bins, c->at<double>(pl.o_nmodes), c->at<double>(pl.o_ksum), nk, ells, n_ells,
-                    c->at<double>(pl.o_derived), P, km, nm, s);
+                    c->at<double>(pl.o_derived), P, km, nm, s, hr.cartesian ? 1 : 0);
   }));
   c->transforms_last = transforms;
   c->sh_last = sh;
@@ -810,6 +842,33 @@ pspec_status pspec_paint(void* ctx, const pspec_catalog* data, const pspec_catal
       return PSPEC_EINVAL;
     }
   }
+  return PSPEC_OK;
+}
+
+pspec_status pspec_multipoles_cartesian(void* ctx, const int32_t* ells, int32_t n_ells, const double* k_edges,
+                                        int32_t n_kbins, double* P, double* k_mean, double* n_modes) {
+  if (!ctx) return PSPEC_EINVAL;
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!P || !k_mean || !n_modes) { c->err = "output pointers are NULL"; return PSPEC_EINVAL; }
+  if (!c->pl.has_ctab) { c->err = "context created without cartesian = 1 (or not FP32)"; return PSPEC_EUNSUPPORTED; }
+  TRY(check_ells_edges(c, ells, n_ells, k_edges, n_kbins));
+  for (int i = 0; i < n_ells; i++)
+    if (ells[i] > 4) { c->err = "the Cartesian route covers l <= 4"; return PSPEC_EUNSUPPORTED; }
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  TRY(upload_bins(c, k_edges, n_kbins));
+  double* out = c->at<double>(c->pl.o_out);
+  const int nk = n_kbins;
+  HRange hr;
+  hr.cartesian = true;
+  TRY(do_multipoles<float>(c, ells, n_ells, nk, out + 2 * (size_t)nk, out, out + nk, hr));
+  std::vector<double> h((size_t)(n_ells + 2) * nk);
+  e = cudaMemcpyAsync(h.data(), out, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "multipoles");
+  std::memcpy(k_mean, h.data(), nk * sizeof(double));
+  std::memcpy(n_modes, h.data() + nk, nk * sizeof(double));
+  std::memcpy(P, h.data() + 2 * (size_t)nk, (size_t)n_ells * nk * sizeof(double));
   return PSPEC_OK;
 }
 
@@ -1138,6 +1197,7 @@ pspec_status pspec_get_plan_info(void* ctx, pspec_plan_info* info) {
   info->kernel_launches = c->launches;
   info->model_bytes_last = c->bytes_paint + c->bytes_mult;
   info->ylm_table_bytes = c->pl.has_ytab ? (int64_t)c->pl.ytab_bytes : 0;
+  info->cartesian_table_bytes = (int64_t)c->pl.ctab_bytes;
   return PSPEC_OK;
 }
 

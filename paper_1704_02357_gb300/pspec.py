@@ -33,7 +33,8 @@ class Params(C.Structure):
                 ("compensate", C.c_int32), ("precision", C.c_int32), ("ell_max", C.c_int32),
                 ("box_size", C.c_double), ("box_corner", C.c_double * 3), ("observer", C.c_double * 3),
                 ("P0", C.c_double), ("nbar", C.c_double), ("max_group_bytes", C.c_int64),
-                ("max_particles", C.c_int64), ("cache_randoms", C.c_int32), ("ylm_table", C.c_int32)]
+                ("max_particles", C.c_int64), ("cache_randoms", C.c_int32), ("ylm_table", C.c_int32),
+                ("cartesian", C.c_int32)]
 
 
 class Catalog(C.Structure):
@@ -56,7 +57,8 @@ class PlanInfo(C.Structure):
                 ("tile_y", C.c_int32), ("tile_x", C.c_int32), ("tile_bin", C.c_int32), ("rows_z", C.c_int32),
                 ("group_max", C.c_int32), ("bin_ctas", C.c_int32), ("sh_transforms", C.c_int64),
                 ("transforms_executed", C.c_int64), ("kernel_launches", C.c_int64),
-                ("model_bytes_last", C.c_double), ("ylm_table_bytes", C.c_int64)]
+                ("model_bytes_last", C.c_double), ("ylm_table_bytes", C.c_int64),
+                ("cartesian_table_bytes", C.c_int64)]
 
 
 _lib = None
@@ -92,6 +94,9 @@ SIGNATURES = [
     ("pspec_set_tuning", C.c_int32, [C.c_void_p, C.POINTER(Tuning)]),
     ("pspec_autotune", C.c_int32, [C.c_void_p, C.POINTER(Catalog), C.POINTER(Catalog), C.POINTER(C.c_int32),
                                    C.c_int32, C.POINTER(C.c_double), C.c_int32, C.c_int32, C.POINTER(Tuning)]),
+    ("pspec_multipoles_cartesian", C.c_int32, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32,
+                                               C.POINTER(C.c_double), C.c_int32, C.POINTER(C.c_double),
+                                               C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("pspec_multipoles_range", C.c_int32, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_double),
                                            C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_void_p]),
     ("pspec_finalize_bins", C.c_int32, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int32), C.c_int32,
@@ -160,7 +165,7 @@ class Estimator:
     def __init__(self, nmesh: int, box_size: float, box_corner, observer=(0.0, 0.0, 0.0), window="cic",
                  interlaced=False, compensate=True, precision="fp32", ell_max=4, P0=0.0, nbar=0.0,
                  max_group_bytes=0, max_kbins=512, max_particles=0, cache_randoms=False, device=None,
-                 stream=None, ylm_table=True):
+                 stream=None, ylm_table=True, cartesian=False):
         import torch
         lib = load()
         self.device = torch.device(device if device is not None else "cuda", )
@@ -171,7 +176,7 @@ class Estimator:
                              PRECISIONS[precision], int(ell_max), float(box_size),
                              (C.c_double * 3)(*box_corner), (C.c_double * 3)(*observer), float(P0), float(nbar),
                              int(max_group_bytes), int(max_particles), int(bool(cache_randoms)),
-                             0 if ylm_table else -1)
+                             0 if ylm_table else -1, int(bool(cartesian)))
         self.max_kbins = int(max_kbins)
         nbytes = C.c_int64(0)
         with torch.cuda.device(self.device):
@@ -212,6 +217,22 @@ class Estimator:
         nm = np.empty(nk)
         dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
         _check(lib.pspec_multipoles(self._ctx, el, len(ells), dp(edges), nk, dp(P), dp(km), dp(nm)), self._ctx)
+        return {"P": P, "k_mean": km, "n_modes": nm, "ells": ells}
+
+    def multipoles_cartesian(self, ells: Sequence[int], k_edges) -> dict:
+        """l in {0, 2, 4} through the Cartesian decomposition (22 transforms for l <= 4); needs
+        an FP32 context created with cartesian=True."""
+        lib = load()
+        ells = [int(e) for e in ells]
+        edges = np.ascontiguousarray(k_edges, dtype=np.float64)
+        nk = len(edges) - 1
+        el = (C.c_int32 * len(ells))(*ells)
+        P = np.empty((len(ells), nk))
+        km = np.empty(nk)
+        nm = np.empty(nk)
+        dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+        _check(lib.pspec_multipoles_cartesian(self._ctx, el, len(ells), dp(edges), nk, dp(P), dp(km), dp(nm)),
+               self._ctx)
         return {"P": P, "k_mean": km, "n_modes": nm, "ells": ells}
 
     def multipoles_device(self, ells: Sequence[int], k_edges, P_out, kmean_out, nmodes_out):

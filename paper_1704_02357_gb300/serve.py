@@ -91,7 +91,7 @@ class Server:
         p = P.Params(nmesh, P.WINDOWS[self.kw["window"]], int(self.kw["interlaced"]), int(self.kw["compensate"]), 0,
                      ell_max, float(self.kw["box_size"]), (C.c_double * 3)(*self.kw["box_corner"]),
                      (C.c_double * 3)(*self.kw["observer"]), float(self.kw["P0"]), float(self.kw["nbar"]),
-                     int(self.max_group_bytes_for(nmesh, ell_max)), self.max_particles, 1, 0)
+                     int(self.max_group_bytes_for(nmesh, ell_max)), self.max_particles, 1, 0, 0)
         n = C.c_int64(0)
         with torch.cuda.device(self.device or torch.cuda.current_device()):
             P._check(lib.pspec_workspace_size(C.byref(p), int(self.kw["max_kbins"]), C.byref(n)))
