@@ -179,6 +179,17 @@ pspec_status pspec_finalize_bins(void* ctx, const double* bins, const int32_t* e
 pspec_status pspec_multipoles_cartesian(void* ctx, const int32_t* ells, int32_t n_ells, const double* k_edges,
                                         int32_t n_kbins, double* P, double* k_mean, double* n_modes);
 
+/* Transverse (mu = 0) systematics, Sec. 3.1 (host functions, FP64, no context needed).
+ * pspec_transverse_response: R(mu) of eq. response, the leakage into P(k, mu) of a spike
+ * P_c(k) delta(mu) reconstructed from the even multipoles up to ell_max:
+ *   R(mu) = -(ell_max+1)/(2 mu) L_ell_max(0) L_{ell_max+1}(mu)  (its limit at mu = 0).
+ * pspec_mu_edges_nonuniform: the ell_max/2 + 2 wedge edges 0 = mu_0 < mu_1 < ... < 1 of eq.
+ * nonuniform-bins, for which the integral of L_{ell_max+1}(mu)/mu over every wedge but the
+ * first vanishes, so that such a spike only enters the first wedge. mu_edges holds
+ * ell_max/2 + 2 doubles (host). ell_max even, 2..16; else PSPEC_EINVAL. */
+pspec_status pspec_transverse_response(int32_t ell_max, const double* mu, int32_t n, double* R);
+pspec_status pspec_mu_edges_nonuniform(int32_t ell_max, double* mu_edges);
+
 /* Batched mocks sharing one randoms catalog (the batching pattern of the mock campaigns
  * that motivate the method, Sec. 1 and Sec. 5). Needs a context created with cache_randoms = 1.
  * pspec_set_randoms paints the randoms once (unscaled) into cached meshes and keeps their

@@ -97,6 +97,8 @@ SIGNATURES = [
     ("pspec_multipoles_cartesian", C.c_int32, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32,
                                                C.POINTER(C.c_double), C.c_int32, C.POINTER(C.c_double),
                                                C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    ("pspec_transverse_response", C.c_int32, [C.c_int32, C.POINTER(C.c_double), C.c_int32, C.POINTER(C.c_double)]),
+    ("pspec_mu_edges_nonuniform", C.c_int32, [C.c_int32, C.POINTER(C.c_double)]),
     ("pspec_multipoles_range", C.c_int32, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_double),
                                            C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_void_p]),
     ("pspec_finalize_bins", C.c_int32, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int32), C.c_int32,
@@ -403,3 +405,19 @@ def catalog_sums_noalloc(params: Params, data_pos, randoms_pos, out, data_weight
                                         C.c_void_p(out.data_ptr()), C.c_void_p(s.cuda_stream))
     _check(st)
     return keep
+
+
+def transverse_response(ell_max: int, mu) -> np.ndarray:
+    """R(mu) of a mu = 0 spike reconstructed from even multipoles up to ell_max (Sec. 3.1)."""
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    out = np.empty_like(mu)
+    dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+    _check(load().pspec_transverse_response(int(ell_max), dp(mu), mu.size, dp(out)))
+    return out
+
+
+def mu_edges_nonuniform(ell_max: int) -> np.ndarray:
+    """Wedge edges confining a mu = 0 spike to the first wedge (Sec. 3.1, ell_max/2 + 1 wedges)."""
+    out = np.empty(int(ell_max) // 2 + 2)
+    _check(load().pspec_mu_edges_nonuniform(int(ell_max), out.ctypes.data_as(C.POINTER(C.c_double))))
+    return out
