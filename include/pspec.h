@@ -190,6 +190,19 @@ pspec_status pspec_multipoles_cartesian(void* ctx, const int32_t* ells, int32_t 
 pspec_status pspec_transverse_response(int32_t ell_max, const double* mu, int32_t n, double* R);
 pspec_status pspec_mu_edges_nonuniform(int32_t ell_max, double* mu_edges);
 
+/* Wedge statistics, Sec. 4.1 (host functions, FP64).
+ * pspec_wedge_lbar: the n_mu x n_ells matrix (row-major, host) of mean Legendre polynomials
+ * over each wedge (eq. Lbar), the map from multipoles to wedges used by pspec_wedges.
+ * pspec_wedge_gamma_kaiser: gamma_mn of eq. gamma, the angular part of the Gaussian covariance
+ * of wedges built from the even multipoles 0..ell_max under the linear Kaiser model
+ * (1 + beta mu^2)^2: sum_{l,l'} (2l+1)(2l'+1) Lbar_l(mu_m) Lbar_l'(mu_n) int dmu/2 L_l L_l'
+ * (1 + beta mu^2)^4, into the host n_mu x n_mu array gamma (row-major). The scale factor
+ * 2 P^2 / N_k of eq. trunc-Cmn is left out. Bad sizes or edges give PSPEC_EINVAL. */
+pspec_status pspec_wedge_lbar(const int32_t* ells, int32_t n_ells, const double* mu_edges, int32_t n_mu,
+                              double* out);
+pspec_status pspec_wedge_gamma_kaiser(int32_t ell_max, const double* mu_edges, int32_t n_mu, double beta,
+                                      double* gamma);
+
 /* Batched mocks sharing one randoms catalog (the batching pattern of the mock campaigns
  * that motivate the method, Sec. 1 and Sec. 5). Needs a context created with cache_randoms = 1.
  * pspec_set_randoms paints the randoms once (unscaled) into cached meshes and keeps their

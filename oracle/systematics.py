@@ -65,3 +65,40 @@ def spike_wedge_ratios(ell_max: int, mu_edges) -> np.ndarray:
         w.append(val / (b - a))
     w = np.array(w)
     return w / w[0]
+
+
+# --------------------------------------------------------------------------- wedge statistics (Sec. 4.1)
+def lbar_matrix(ells, mu_edges) -> np.ndarray:
+    """(n_mu, n_ells) mean of L_l over each wedge, by numerical quadrature."""
+    e = np.asarray(mu_edges, dtype=np.float64)
+    out = np.empty((len(e) - 1, len(ells)))
+    for w, (a, b) in enumerate(zip(e[:-1], e[1:])):
+        for i, ell in enumerate(ells):
+            val, _ = integrate.quad(lambda m: special.eval_legendre(ell, m), a, b, epsabs=1e-14)
+            out[w, i] = val / (b - a)
+    return out
+
+
+def gamma_kaiser(ell_max: int, mu_edges, beta: float) -> np.ndarray:
+    """gamma_mn of eq. gamma over the even multipoles 0..l_max, the mu integrals by quadrature."""
+    ells = list(range(0, ell_max + 1, 2))
+    Lb = lbar_matrix(ells, mu_edges)
+    I = np.empty((len(ells), len(ells)))
+    for a, la in enumerate(ells):
+        for b, lb in enumerate(ells):
+            f = lambda m: 0.5 * special.eval_legendre(la, m) * special.eval_legendre(lb, m) * (1 + beta * m * m) ** 4
+            I[a, b], _ = integrate.quad(f, -1.0, 1.0, epsabs=1e-14, limit=200)
+    D = np.array([2 * l + 1 for l in ells], dtype=np.float64)
+    M = Lb * D[None, :]
+    return M @ I @ M.T
+
+
+def condition_number(M) -> float:
+    """Smallest over largest singular value (the paper's definition, Sec. 4.1)."""
+    s = np.linalg.svd(np.asarray(M, dtype=np.float64), compute_uv=False)
+    return float(s.min() / s.max())
+
+
+def correlation(C) -> np.ndarray:
+    d = np.sqrt(np.diag(C))
+    return C / np.outer(d, d)

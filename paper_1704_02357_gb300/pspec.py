@@ -99,6 +99,10 @@ SIGNATURES = [
                                                C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("pspec_transverse_response", C.c_int32, [C.c_int32, C.POINTER(C.c_double), C.c_int32, C.POINTER(C.c_double)]),
     ("pspec_mu_edges_nonuniform", C.c_int32, [C.c_int32, C.POINTER(C.c_double)]),
+    ("pspec_wedge_lbar", C.c_int32, [C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_double), C.c_int32,
+                                     C.POINTER(C.c_double)]),
+    ("pspec_wedge_gamma_kaiser", C.c_int32, [C.c_int32, C.POINTER(C.c_double), C.c_int32, C.c_double,
+                                             C.POINTER(C.c_double)]),
     ("pspec_multipoles_range", C.c_int32, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_double),
                                            C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_void_p]),
     ("pspec_finalize_bins", C.c_int32, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int32), C.c_int32,
@@ -420,4 +424,24 @@ def mu_edges_nonuniform(ell_max: int) -> np.ndarray:
     """Wedge edges confining a mu = 0 spike to the first wedge (Sec. 3.1, ell_max/2 + 1 wedges)."""
     out = np.empty(int(ell_max) // 2 + 2)
     _check(load().pspec_mu_edges_nonuniform(int(ell_max), out.ctypes.data_as(C.POINTER(C.c_double))))
+    return out
+
+
+def wedge_lbar(ells: Sequence[int], mu_edges) -> np.ndarray:
+    """(n_mu, n_ells) mean Legendre polynomials over each wedge (Sec. 2.2 eq. Lbar)."""
+    mu = np.ascontiguousarray(mu_edges, dtype=np.float64)
+    ells = [int(e) for e in ells]
+    out = np.empty((len(mu) - 1, len(ells)))
+    el = (C.c_int32 * len(ells))(*ells)
+    dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+    _check(load().pspec_wedge_lbar(el, len(ells), dp(mu), len(mu) - 1, dp(out)))
+    return out
+
+
+def wedge_gamma_kaiser(ell_max: int, mu_edges, beta: float) -> np.ndarray:
+    """gamma_mn of Sec. 4.1 (Kaiser-model wedge covariance, angular part)."""
+    mu = np.ascontiguousarray(mu_edges, dtype=np.float64)
+    out = np.empty((len(mu) - 1, len(mu) - 1))
+    dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+    _check(load().pspec_wedge_gamma_kaiser(int(ell_max), dp(mu), len(mu) - 1, float(beta), dp(out)))
     return out
