@@ -71,7 +71,10 @@ typedef struct {
   int32_t nmesh;           /* N: even, 8 <= N <= 1024, N = 2^a or 3*2^a */
   int32_t window;          /* PSPEC_WINDOW_CIC or PSPEC_WINDOW_TSC */
   int32_t interlaced;      /* 0/1: paint a second mesh shifted by H/2 (Sec. 2.3) */
-  int32_t compensate;      /* 0/1: divide by prod_d sinc^p(pi n_d/N) */
+  int32_t compensate;      /* 0: none; 1: divide by prod_d sinc^p(pi n_d/N); 2: divide by
+                              prod_d sqrt(C_p(n_d)), C_p the alias sum of sinc^{2p} in the
+                              closed form of Jing (2005) (removes the aliased shot noise of a
+                              non-interlaced mesh on average) */
   int32_t precision;       /* PSPEC_FP32 (FP32 meshes/transforms, FP64 sums and bins) or PSPEC_FP64 */
   int32_t ell_max;         /* largest even l this context will be asked for, <= 16 */
   double box_size;         /* L */

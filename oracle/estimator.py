@@ -67,6 +67,7 @@ class Params:
     compensate: bool = True
     P0: float = 0.0          # FKP P0; 0 means w_fkp = 1
     nbar: float = 0.0        # n̄ used when a catalog carries none
+    compensation: str = "sinc"  # "sinc": prod_d sinc^p; "jing": the alias-summed form of Jing (2005)
 
     @property
     def cell(self) -> float:
@@ -172,12 +173,23 @@ def nyquist_mask(n: int) -> np.ndarray:
     return fx | fy | fz
 
 
-def window_transfer(n: int, window: str) -> np.ndarray:
-    """W(k) = prod_d sinc^p(pi n_d / N) over the half spectrum (Sec. 2.3 compensation)."""
+def window_transfer(n: int, window: str, form: str = "sinc") -> np.ndarray:
+    """The compensation divisor over the half spectrum (Sec. 2.3, which cites Jing 2005).
+
+    "sinc": W(k) = prod_d sinc^p(pi n_d / N). "jing": prod_d sqrt(C_p(n_d)), C_p the sum of
+    sinc^{2p} over the aliases n_d + m N, in its closed form for CIC (1 - 2/3 s^2) and TSC
+    (1 - s^2 + 2/15 s^4), s = sin(pi n_d / N): dividing the field by it removes the aliased
+    shot noise of a non-interlaced mesh on average."""
     p = WINDOW_ORDER[window]
     full, half = int_freqs(n)
-    sx = np.sinc(full / n) ** p       # numpy sinc(x) = sin(pi x)/(pi x)
-    sz = np.sinc(half / n) ** p
+
+    def axis(v):
+        if form == "sinc":
+            return np.sinc(v / n) ** p    # numpy sinc(x) = sin(pi x)/(pi x)
+        s2 = np.sin(np.pi * v / n) ** 2
+        c = 1.0 - 2.0 / 3.0 * s2 if p == 2 else 1.0 - s2 + 2.0 / 15.0 * s2 * s2
+        return np.sqrt(c)
+    sx, sz = axis(full), axis(half)
     return sx[:, None, None] * sx[None, :, None] * sz[None, None, :]
 
 
@@ -292,7 +304,7 @@ def density_fields(data, randoms, params: Params) -> Fields:
     else:
         X = F1
     if params.compensate:
-        X = X / window_transfer(n, params.window)
+        X = X / window_transfer(n, params.window, params.compensation)
     if params.interlaced or params.compensate:
         X = np.where(nyquist_mask(n), 0.0, X)
         f = sfft.irfftn(X, s=(n, n, n), workers=_workers())

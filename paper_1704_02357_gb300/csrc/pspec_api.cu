@@ -67,6 +67,7 @@ pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl,
   if (!p) { *why = "params is NULL"; return PSPEC_EINVAL; }
   if (!good_nmesh(p->nmesh)) { *why = "nmesh must be even, 16..1024 and 2^a, or 48..768 and 3*2^a"; return PSPEC_EUNSUPPORTED; }
   if (p->window != PSPEC_WINDOW_CIC && p->window != PSPEC_WINDOW_TSC) { *why = "window must be CIC or TSC"; return PSPEC_EINVAL; }
+  if (p->compensate < 0 || p->compensate > 2) { *why = "compensate must be 0, 1 or 2"; return PSPEC_EINVAL; }
   if (p->precision != PSPEC_FP32 && p->precision != PSPEC_FP64) { *why = "precision must be FP32 or FP64"; return PSPEC_EINVAL; }
   if (p->ell_max < 0 || (p->ell_max & 1)) { *why = "ell_max must be even and >= 0"; return PSPEC_EUNSUPPORTED; }
   if (p->ell_max > PSPEC_MAX_ELL) { *why = "ell_max > 16"; return PSPEC_EUNSUPPORTED; }
@@ -294,9 +295,16 @@ pspec_status upload_tables(Ctx* c) {
   for (int d = 0; d < 3; d++)
     for (int i = 0; i < N; i++) axis[d * N + i] = T(c->p.box_corner[d] + i * H - c->p.observer[d]);
   const int p = c->p.window;  // order of sinc^p
+  // compensation divisor per axis: sinc^p(pi n/N), or (compensate = 2) the square root of its
+  // alias sum sum_m sinc^{2p}(pi (n/N + m)) in closed form (Jing 2005): 1 - 2/3 s^2 (CIC),
+  // 1 - s^2 + 2/15 s^4 (TSC), s = sin(pi n/N)
   auto sincp = [&](int n) {
-    if (n == 0) return 1.0;
     const double x = M_PI * n / N;
+    if (c->p.compensate == 2) {
+      const double s2 = std::sin(x) * std::sin(x);
+      return std::sqrt(p == PSPEC_WINDOW_CIC ? 1.0 - 2.0 / 3.0 * s2 : 1.0 - s2 + 2.0 / 15.0 * s2 * s2);
+    }
+    if (n == 0) return 1.0;
     return std::pow(std::sin(x) / x, p);
   };
   // exp(-i pi s / N), s = nx + ny + nz in [-3N/2, 3N/2): the H/2 shift of the second mesh

@@ -178,7 +178,8 @@ class Estimator:
         if self.device.index is None:
             self.device = torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        self.params = Params(int(nmesh), WINDOWS[window], int(bool(interlaced)), int(bool(compensate)),
+        comp = 2 if compensate == "jing" else (1 if compensate in (True, "sinc", 1) else 0)
+        self.params = Params(int(nmesh), WINDOWS[window], int(bool(interlaced)), comp,
                              PRECISIONS[precision], int(ell_max), float(box_size),
                              (C.c_double * 3)(*box_corner), (C.c_double * 3)(*observer), float(P0), float(nbar),
                              int(max_group_bytes), int(max_particles), int(bool(cache_randoms)),
