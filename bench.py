@@ -410,6 +410,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the l<=16 and FP64 side measurements")
     ap.add_argument("--nmesh", type=int, default=NMESH, help="mesh side (512 is the benchmark; smaller for ncu captures)")
     ap.add_argument("--ells", default="0,2,4", help="multipoles of the headline measurement")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's default knobs (profiling runs: no candidate launches)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -487,7 +489,7 @@ def main():
     # ---- headline: FP32, l = 0, 2, 4 (knobs from the autotuner, cached per GPU and plan shape)
     est = est_for("fp32", max(ells_main))
     from paper_1704_02357_gb300 import tune
-    tuning = tune.tuned(est, dpos, rpos, ells_main, edges)
+    tuning = est.tuning() if args.no_autotune else tune.tuned(est, dpos, rpos, ells_main, edges)
     uuid = None
     try:
         uuid = str(torch.cuda.get_device_properties(dev).uuid)
