@@ -74,7 +74,9 @@ typedef struct {
   int32_t compensate;      /* 0: none; 1: divide by prod_d sinc^p(pi n_d/N); 2: divide by
                               prod_d sqrt(C_p(n_d)), C_p the alias sum of sinc^{2p} in the
                               closed form of Jing (2005) (removes the aliased shot noise of a
-                              non-interlaced mesh on average) */
+                              non-interlaced mesh on average); 3: leave the field uncompensated
+                              and divide each mode's binned product by prod_d sinc^{2p} (no
+                              inverse transform without interlacing) */
   int32_t precision;       /* PSPEC_FP32 (FP32 meshes/transforms, FP64 sums and bins) or PSPEC_FP64 */
   int32_t ell_max;         /* largest even l this context will be asked for, <= 16 */
   double box_size;         /* L */

@@ -184,7 +184,7 @@ def window_transfer(n: int, window: str, form: str = "sinc") -> np.ndarray:
     full, half = int_freqs(n)
 
     def axis(v):
-        if form == "sinc":
+        if form in ("sinc", "sinc_per_mode"):
             return np.sinc(v / n) ** p    # numpy sinc(x) = sin(pi x)/(pi x)
         s2 = np.sin(np.pi * v / n) ** 2
         c = 1.0 - 2.0 / 3.0 * s2 if p == 2 else 1.0 - s2 + 2.0 / 15.0 * s2 * s2
@@ -303,9 +303,12 @@ def density_fields(data, randoms, params: Params) -> Fields:
         del F2
     else:
         X = F1
-    if params.compensate:
+    # "sinc_per_mode": the field is left uncompensated and each mode's binned product is
+    # divided by W(k)^2 instead (multipoles_from_fields)
+    field_comp = params.compensate and params.compensation != "sinc_per_mode"
+    if field_comp:
         X = X / window_transfer(n, params.window, params.compensation)
-    if params.interlaced or params.compensate:
+    if params.interlaced or field_comp:
         X = np.where(nyquist_mask(n), 0.0, X)
         f = sfft.irfftn(X, s=(n, n, n), workers=_workers())
     else:
@@ -340,6 +343,10 @@ def multipoles_from_fields(fl: Fields, params: Params, ells: Sequence[int], k_ed
         k_mean = ksum / n_modes
     I, S = fl.sums["I"], fl.sums["S"]
     F0 = fl.F0
+    # compensation per mode: 1/W^2 on every binned product
+    wm = (1.0 / window_transfer(n, params.window, "sinc")[sel] ** 2
+          if params.compensate and params.compensation == "sinc_per_mode" else 1.0)
+    ms = ms * wm
     P = np.zeros((len(ells), nk))
     khat = None
     for li, ell in enumerate(ells):

@@ -70,6 +70,15 @@ __device__ __forceinline__ void row_mirrors(const C (&v)[E], C (&zm)[E], int t) 
   }
 }
 
+// v / W(k)^2 for the mode (ii, j, kz), 1/W = prod_d hi_d (1 + lo_d) from the per-axis table: the
+// relative errors lo_d enter the rounding of the exact product v * p^2 (compensation per mode).
+template <typename T, int N>
+__device__ __forceinline__ T per_mode_w2(T v, const cx<T>* __restrict__ iw, int ii, int j, int kz) {
+  const cx<T> a = iw[ii], b = iw[j], c = iw[N + kz];
+  const T p = a.x * b.x * c.x, p2 = p * p, l2 = T(2) * (a.y + b.y + c.y);
+  return fma_t(v, p2, v * p2 * l2);
+}
+
 // ------------------------------------------------------------------ pass z: r2c of plain rows
 template <typename T, int N>
 __global__ void __launch_bounds__(Shape<N>::ZT, min_blocks<T, Shape<N>::E>(Shape<N>::ZT))
@@ -338,7 +347,7 @@ __global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T, Shape<N>::E>(Shape
         const C A = F0[addr];
         X = cscale(cadd(A, umul(X, ldg_u(phase + syz + sfreq<N>(ii)))), T(0.5));
       }
-      if (compensate) {
+      if (compensate == 1 || compensate == 2) {
         // 1/W = prod_d hi_d (1 + lo_d): the relative rounding errors lo_d of the per-axis
         // factors enter the roundings of the products X * w3, so that no per-axis
         // deterministic error is left on the modes
@@ -353,7 +362,11 @@ __global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T, Shape<N>::E>(Shape
         const int nx = sfreq<N>(ii);
         const int n2 = nx * nx + ny * ny + kz * kz;
         const int b = ba.bin_of_n2[n2];
-        if (b >= 0 && n2 > 0) wb.add(b, mult * (X.x * X.x + X.y * X.y));
+        if (b >= 0 && n2 > 0) {
+          T x2 = X.x * X.x + X.y * X.y;
+          if (compensate == 3) x2 = per_mode_w2<T, N>(x2, invw, ii, j, kz);  // compensation per mode
+          wb.add(b, mult * x2);
+        }
       }
     }
     __syncthreads();
@@ -451,7 +464,12 @@ __global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T, Shape<N>::E>(Shape
         const int nx = sfreq<N>(ii);
         const int n2 = nx * nx + ny * ny + kz * kz;
         const int b = ba.bin_of_n2[n2];
-        if (b >= 0 && n2 > 0) wb.add(b, mult * acc[e]);
+        if (b >= 0 && n2 > 0) {
+          auto a = acc[e];
+          using V = decltype(a);
+          if (ba.permode_w) a = per_mode_w2<V, N>(a, static_cast<const cx<V>*>(ba.permode_w), ii, j, kz);
+          wb.add(b, mult * a);
+        }
       }
     }
     __syncthreads();
@@ -561,7 +579,12 @@ __global__ void __launch_bounds__(Shape<N>::CT, min_blocks<float, Shape<N>::E>(S
         const int nx = sfreq<N>(ii);
         const int n2 = nx * nx + ny * ny + kz * kz;
         const int b = ba.bin_of_n2[n2];
-        if (b >= 0 && n2 > 0) wb.add(b, mult * acc[e]);
+        if (b >= 0 && n2 > 0) {
+          auto a = acc[e];
+          using V = decltype(a);
+          if (ba.permode_w) a = per_mode_w2<V, N>(a, static_cast<const cx<V>*>(ba.permode_w), ii, j, kz);
+          wb.add(b, mult * a);
+        }
       }
     }
     __syncthreads();

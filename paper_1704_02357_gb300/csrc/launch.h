@@ -49,6 +49,7 @@ struct BinArgs {
   const int32_t* bin_of_n2;  // bin index of |n|^2, or -1
   int nk;
   double* bins;              // [slots][nk] FP64 sums, added to with atomics
+  const void* permode_w;     // compensation applied per mode in the binning (cx<T> per-axis table), or nullptr
 };
 
 // a1: per-block partial sums of one weighted catalog; final combine into `derived`.

@@ -67,7 +67,7 @@ pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl,
   if (!p) { *why = "params is NULL"; return PSPEC_EINVAL; }
   if (!good_nmesh(p->nmesh)) { *why = "nmesh must be even, 16..1024 and 2^a, or 48..768 and 3*2^a"; return PSPEC_EUNSUPPORTED; }
   if (p->window != PSPEC_WINDOW_CIC && p->window != PSPEC_WINDOW_TSC) { *why = "window must be CIC or TSC"; return PSPEC_EINVAL; }
-  if (p->compensate < 0 || p->compensate > 2) { *why = "compensate must be 0, 1 or 2"; return PSPEC_EINVAL; }
+  if (p->compensate < 0 || p->compensate > 3) { *why = "compensate must be 0..3"; return PSPEC_EINVAL; }
   if (p->precision != PSPEC_FP32 && p->precision != PSPEC_FP64) { *why = "precision must be FP32 or FP64"; return PSPEC_EINVAL; }
   if (p->ell_max < 0 || (p->ell_max & 1)) { *why = "ell_max must be even and >= 0"; return PSPEC_EUNSUPPORTED; }
   if (p->ell_max > PSPEC_MAX_ELL) { *why = "ell_max > 16"; return PSPEC_EUNSUPPORTED; }
@@ -93,7 +93,9 @@ pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl,
   pl->tf = pass_table<float>(N);
   pl->td = pass_table<double>(N);
   if (!pl->tf || !pl->td) { *why = "no compiled transform passes for this nmesh"; return PSPEC_EUNSUPPORTED; }
-  pl->roundtrip = p->interlaced || p->compensate;
+  // the inverse transform is needed for interlacing, and for compensation of the field; with
+  // compensation per mode (3) the painted mesh itself is weighted
+  pl->roundtrip = p->interlaced || p->compensate == 1 || p->compensate == 2;
   pl->Sr = (size_t)N * N * N * pl->esz;
   pl->Sc = (size_t)N * N * NH * csz;
   pl->n2max = 3 * NH * NH;
@@ -518,6 +520,7 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
   ba.bin_of_n2 = c->at<int32_t>(pl.o_bin);
   ba.nk = nk;
   ba.bins = c->at<double>(pl.o_bins);
+  ba.permode_w = c->p.compensate == 3 ? static_cast<const void*>(c->at<C>(pl.o_invw)) : nullptr;
   cudaError_t e = cudaMemsetAsync(ba.bins, 0, (size_t)(SLOT_ELL0 + std::max(n_ells, 2)) * nk * sizeof(double), s);
   if (e != cudaSuccess) return cuda_fail(c, e, "bins clear");
   int64_t transforms = 0;

@@ -112,6 +112,14 @@ SIGNATURES = [
 ]
 
 
+def compensation_code(compensate) -> int:
+    """False/True, or a form: "sinc" (1), "jing" (2), "sinc_per_mode" (3, 1/W^2 on each binned mode)."""
+    codes = {False: 0, True: 1, 0: 0, 1: 1, 2: 2, 3: 3, "sinc": 1, "jing": 2, "sinc_per_mode": 3}
+    if compensate not in codes:
+        raise ValueError(f"unknown compensation {compensate!r}")
+    return codes[compensate]
+
+
 def load(path: str = LIB_PATH):
     """Load libpspec.so and declare its signatures. Raises if it is not built."""
     global _lib
@@ -178,7 +186,7 @@ class Estimator:
         if self.device.index is None:
             self.device = torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        comp = 2 if compensate == "jing" else (1 if compensate in (True, "sinc", 1) else 0)
+        comp = compensation_code(compensate)
         self.params = Params(int(nmesh), WINDOWS[window], int(bool(interlaced)), comp,
                              PRECISIONS[precision], int(ell_max), float(box_size),
                              (C.c_double * 3)(*box_corner), (C.c_double * 3)(*observer), float(P0), float(nbar),

@@ -88,8 +88,7 @@ class Server:
         import ctypes as C
         import torch
         lib = P.load()
-        comp = self.kw["compensate"]
-        comp = 2 if comp == "jing" else (1 if comp in (True, "sinc", 1) else 0)
+        comp = P.compensation_code(self.kw["compensate"])
         p = P.Params(nmesh, P.WINDOWS[self.kw["window"]], int(self.kw["interlaced"]), comp, 0,
                      ell_max, float(self.kw["box_size"]), (C.c_double * 3)(*self.kw["box_corner"]),
                      (C.c_double * 3)(*self.kw["observer"]), float(self.kw["P0"]), float(self.kw["nbar"]),

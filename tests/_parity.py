@@ -9,7 +9,7 @@ from oracle import estimator as E
 
 def gpu_estimator(p: E.Params, precision="fp32", ell_max=4, max_kbins=512, **kw):
     from paper_1704_02357_gb300 import Estimator
-    comp = ("jing" if p.compensation == "jing" else True) if p.compensate else False
+    comp = p.compensation if p.compensate else False
     return Estimator(nmesh=p.nmesh, box_size=p.box_size, box_corner=p.box_corner, observer=p.observer,
                      window=p.window, interlaced=p.interlaced, compensate=comp, precision=precision,
                      ell_max=ell_max, P0=p.P0, nbar=p.nbar, max_kbins=max_kbins, **kw)

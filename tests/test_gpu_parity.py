@@ -324,13 +324,15 @@ def test_ylm_table_and_per_mode_paths_match_oracle():
     assert g["plan"]["ylm_table_bytes"] == 0
 
 
+@pytest.mark.parametrize("form", ["jing", "sinc_per_mode"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("nmesh,window,interlaced", [(32, "cic", False), (48, "tsc", True)])
-def test_jing_compensation_matches_oracle(precision, nmesh, window, interlaced):
-    """compensate = 2: the alias-summed divisor of Jing (2005) in place of prod sinc^p."""
+def test_compensation_forms_match_oracle(form, precision, nmesh, window, interlaced):
+    """compensate = 2: the alias-summed divisor of Jing (2005) in place of prod sinc^p;
+    compensate = 3: the field left as painted and 1/W^2 applied to each binned mode."""
     from dataclasses import replace
     d, r, p, edges = _offnode(nmesh, window, interlaced, seed=31)
-    p = replace(p, compensation="jing")
+    p = replace(p, compensation=form)
     ells = [0, 2, 4]
     o = E.multipoles(d, r, p, ells, edges)
     g = run_gpu(p, d, r, ells, edges, precision=precision)
@@ -339,6 +341,7 @@ def test_jing_compensation_matches_oracle(precision, nmesh, window, interlaced):
         np.testing.assert_allclose(g["P"], o["P"], rtol=1e-8, atol=1e-10 * scale.max())
     else:
         check_fp32(g, o, ells, scale=scale)
-    # and it differs from the sinc form (the test has teeth)
-    o_sinc = E.multipoles(d, r, replace(p, compensation="sinc"), [0], edges)
-    assert np.max(np.abs(o_sinc["P"][0] - o["P"][0]) / scale) > 1e-3
+    # and it differs from the field-level sinc form (the test has teeth)
+    o_sinc = E.multipoles(d, r, replace(p, compensation="sinc"), ells, edges)
+    k = 0 if form == "jing" else 1  # per mode, l = 0 is identical by construction
+    assert np.max(np.abs(o_sinc["P"][k] - o["P"][k]) / scale) > 1e-4

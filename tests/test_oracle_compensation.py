@@ -43,3 +43,31 @@ def test_jing_compensation_flattens_the_aliased_shot_noise():
     expect = np.sum((mult * ratio)[top]) / np.sum(mult[top])
     assert expect > 0.15
     assert abs(res["sinc"][-1] - expect) < 0.05
+
+
+def _offnode_case(observer):
+    L, n = 400.0, 16
+    d = synth.uniform_box(800, L, (0.0, 0.0, 0.0), 5)
+    r = synth.uniform_box(3000, L, (0.0, 0.0, 0.0), 6)
+    edges = np.linspace(0.0, math.pi * n / L, 6)
+    return d, r, L, n, edges
+
+
+@pytest.mark.parametrize("interlaced", [False, True])
+def test_per_mode_compensation_equals_field_compensation_where_it_must(interlaced):
+    """|X/W|^2 = |X|^2/W^2, so P_0 agrees for any observer; in the distant-observer limit
+    Y_lm(rhat) is constant and every P_l agrees; with a near observer P_2 differs."""
+    from dataclasses import replace
+    ells = [0, 2, 4]
+    for obs, all_equal in (((-300.0, -200.0, -250.0), False), ((200.0, 200.0, -1e13), True)):
+        d, r, L, n, edges = _offnode_case(obs)
+        p = E.Params(nmesh=n, box_size=L, box_corner=(0, 0, 0), observer=obs, window="tsc", interlaced=interlaced,
+                     compensate=True, P0=1e4, nbar=800 / L ** 3)
+        a = E.multipoles(d, r, p, ells, edges)
+        b = E.multipoles(d, r, replace(p, compensation="sinc_per_mode"), ells, edges)
+        scale = np.max(np.abs(a["P"][0]) + a["S"] / a["I"])
+        np.testing.assert_allclose(b["P"][0], a["P"][0], rtol=1e-10, atol=1e-12 * scale)
+        if all_equal:
+            np.testing.assert_allclose(b["P"], a["P"], rtol=1e-6, atol=1e-8 * scale)
+        else:
+            assert np.max(np.abs(b["P"][1] - a["P"][1])) > 1e-4 * scale
