@@ -121,6 +121,45 @@ template <typename C> struct Dft<C, 8> {
   }
 };
 
+// 16 = 4 x 4: four DFT4 over n1 (inputs n2 + 4 n1), twiddles W16^(n2 k1), four DFT4 over n2;
+// output k1 + 4 k2. Irrational constants as hi + lo (ConstMul), as in the radix-8 butterfly.
+template <typename C> struct Dft<C, 16> {
+  static __device__ __forceinline__ void run(C* v, int dir) {
+    using T = typename BaseOf<C>::type;
+    const ConstMul<T> h(0.70710678118654752440), c1(0.92387953251128675613), s1(0.38268343236508977173);
+    C a[4][4];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; n2++) {
+      C t[4] = {v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]};
+      Dft<C, 4>::run(t, dir);
+#pragma unroll
+      for (int k1 = 0; k1 < 4; k1++) a[n2][k1] = t[k1];
+    }
+    // W16^m = cos(2 pi m/16) + i dir sin(2 pi m/16) for m = n2 k1
+    const T d = T(dir);
+    auto rot = [&](C z, const ConstMul<T>& cr, const ConstMul<T>& ci, T sr, T si) {  // z * (sr cr + i si ci)
+      const T re = sr * cr(z.x) - si * ci(z.y), im = sr * cr(z.y) + si * ci(z.x);
+      return mk(re, im);
+    };
+    a[1][1] = rot(a[1][1], c1, s1, T(1), d);                                       // m = 1
+    a[1][2] = mk(h(a[1][2].x - d * a[1][2].y), h(a[1][2].y + d * a[1][2].x));      // m = 2
+    a[1][3] = rot(a[1][3], s1, c1, T(1), d);                                       // m = 3
+    a[2][1] = mk(h(a[2][1].x - d * a[2][1].y), h(a[2][1].y + d * a[2][1].x));      // m = 2
+    a[2][2] = cmul_i(a[2][2], dir);                                                // m = 4
+    a[2][3] = mk(h(-a[2][3].x - d * a[2][3].y), h(-a[2][3].y + d * a[2][3].x));    // m = 6
+    a[3][1] = rot(a[3][1], s1, c1, T(1), d);                                       // m = 3
+    a[3][2] = mk(h(-a[3][2].x - d * a[3][2].y), h(-a[3][2].y + d * a[3][2].x));    // m = 6
+    a[3][3] = rot(a[3][3], c1, s1, T(-1), -d);                                     // m = 9
+#pragma unroll
+    for (int k1 = 0; k1 < 4; k1++) {
+      C t[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
+      Dft<C, 4>::run(t, dir);
+#pragma unroll
+      for (int k2 = 0; k2 < 4; k2++) v[k1 + 4 * k2] = t[k2];
+    }
+  }
+};
+
 template <typename C> struct Dft<C, 3> {
   static __device__ __forceinline__ void run(C* v, int dir) {
     using T = typename BaseOf<C>::type;

@@ -28,12 +28,20 @@ struct CtPlan {
   int ns[12];
 };
 
-__host__ __device__ constexpr CtPlan ct_plan(int L) {
+// Radices in order 16 (only when a thread holds a multiple of 16 elements), 8, 4, 2, then 3.
+__host__ __device__ constexpr CtPlan ct_plan(int L, int E = 8) {
   CtPlan p{0, {0}, {0}};
   int x = L, ns = 1, three = 0;
   while (x % 3 == 0) {
     x /= 3;
     three++;
+  }
+  while (E % 16 == 0 && x % 16 == 0) {
+    p.rad[p.nst] = 16;
+    p.ns[p.nst] = ns;
+    ns *= 16;
+    x /= 16;
+    p.nst++;
   }
   while (x % 8 == 0) {
     p.rad[p.nst] = 8;
@@ -153,7 +161,7 @@ template <bool WARP> __device__ __forceinline__ void fft_sync() {
 // (kInterleaved only).
 template <typename C, int E, int L, int LAYOUT, int NSEQ, int DIR, bool WARP = false>
 __device__ __forceinline__ void fft_ct(C (&v)[E], C* sm, int t, int seq, const ux_of<C>* __restrict__ tw) {
-  constexpr CtPlan P = ct_plan(L);
+  constexpr CtPlan P = ct_plan(L, E);
   constexpr int Tc = L / E;
   static_assert(!WARP || (LAYOUT == kPaddedRows && Tc <= 32 && 32 % Tc == 0), "warp-synchronous rows only");
   static_for<0, P.nst>([&](auto s_) {

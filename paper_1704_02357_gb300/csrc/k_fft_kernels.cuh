@@ -25,7 +25,8 @@ namespace pspec {
 template <int N> struct Shape {
   static constexpr int NH = N / 2;
   static constexpr int E = elems_for(N);
-  static constexpr int Tz = NH / E;      // threads per row in the z passes
+  static constexpr int EZ = z_elems(N);  // elements per thread in the z passes
+  static constexpr int Tz = NH / EZ;     // threads per row in the z passes
   static constexpr bool ZW = Tz <= 32;   // a z row within one warp: warp-level barriers suffice
   static constexpr int Tc = N / E;       // threads per column in the y / x passes
   static constexpr int TW = col_tile(N); // kz columns per tile
@@ -81,12 +82,12 @@ __device__ __forceinline__ T per_mode_w2(T v, const cx<T>* __restrict__ iw, int 
 
 // ------------------------------------------------------------------ pass z: r2c of plain rows
 template <typename T, int N>
-__global__ void __launch_bounds__(Shape<N>::ZT, min_blocks<T, Shape<N>::E>(Shape<N>::ZT))
+__global__ void __launch_bounds__(Shape<N>::ZT, min_blocks<T, Shape<N>::EZ>(Shape<N>::ZT))
     k_r2c_z(const T* __restrict__ in, cx<T>* __restrict__ out, const ux<T>* __restrict__ twh,
             const ux<T>* __restrict__ twr) {
   using C = cx<T>;
   using S = Shape<N>;
-  constexpr int L = S::NH, E = S::E, Tc = S::Tz;
+  constexpr int L = S::NH, E = S::EZ, Tc = S::Tz;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int r = threadIdx.x / Tc, t = threadIdx.x - r * Tc;
@@ -120,12 +121,12 @@ __global__ void __launch_bounds__(Shape<N>::ZT, min_blocks<T, Shape<N>::E>(Shape
 // ------------------------------------------------------------------ pass z: c2r
 // Rows of L stored modes (the kz = N/2 mode taken as 0) -> N reals, times `scale`.
 template <typename T, int N>
-__global__ void __launch_bounds__(Shape<N>::ZT, min_blocks<T, Shape<N>::E>(Shape<N>::ZT))
+__global__ void __launch_bounds__(Shape<N>::ZT, min_blocks<T, Shape<N>::EZ>(Shape<N>::ZT))
     k_c2r_z(const cx<T>* __restrict__ in, T* __restrict__ out, const ux<T>* __restrict__ twh,
             const ux<T>* __restrict__ twr, T scale) {
   using C = cx<T>;
   using S = Shape<N>;
-  constexpr int L = S::NH, E = S::E, Tc = S::Tz;
+  constexpr int L = S::NH, E = S::EZ, Tc = S::Tz;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int r = threadIdx.x / Tc, t = threadIdx.x - r * Tc;
@@ -161,7 +162,7 @@ __global__ void __launch_bounds__(512) k_ylm_r2c_z(const T* __restrict__ f, cx<T
                                                   const __grid_constant__ YTab<T> yt) {
   using C = cx<T>;
   using S = Shape<N>;
-  constexpr int L = S::NH, E = S::E, Tc = S::Tz;
+  constexpr int L = S::NH, E = S::EZ, Tc = S::Tz;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* stage = reinterpret_cast<T*>(smraw);  // [nseq][N] reals, then the exchange buffer
   C* xb = reinterpret_cast<C*>(smraw);

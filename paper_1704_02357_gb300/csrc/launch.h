@@ -109,8 +109,11 @@ constexpr int col_tile(int N) {
   while (tw * 2 <= cap && (N / 2) % (tw * 2) == 0 && N * tw * 2 <= 4096) tw *= 2;
   return tw;
 }
+// Elements per thread in the z passes (rows of N/2 complex points): 16 where a row splits into
+// radix-16 stages (one exchange fewer than radix 8 for 256 points), else as elsewhere.
+constexpr int z_elems(int N) { return N % 3 == 0 ? 24 : (N / 2 >= 128 ? 16 : 8); }
 constexpr int z_rows(int N) {
-  const int tz = (N / 2) / elems_per_thread(N);
+  const int tz = (N / 2) / z_elems(N);
   int cap = 512 / tz, r = 1;
   while (r * 2 <= cap && ((long long)N * N) % (r * 2) == 0) r *= 2;
   return r;
