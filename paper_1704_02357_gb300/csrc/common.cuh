@@ -160,6 +160,41 @@ template <typename C> struct Dft<C, 16> {
   }
 };
 
+// 32 = 2 x 16: two DFT16 over the even and odd inputs, twiddles W32^k1 on the odd half (hi/lo
+// constants), one DFT2 per k1; output k1 + 16 k2.
+template <typename C> struct Dft<C, 32> {
+  static __device__ __forceinline__ void run(C* v, int dir) {
+    using T = typename BaseOf<C>::type;
+    C e[16], o[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+      e[i] = v[2 * i];
+      o[i] = v[2 * i + 1];
+    }
+    Dft<C, 16>::run(e, dir);
+    Dft<C, 16>::run(o, dir);
+    // cos(2 pi k/32), k = 0..8 (sin(2 pi k/32) = cos(2 pi (8-k)/32))
+    constexpr double kc[9] = {1.0, 0.98078528040323044913, 0.92387953251128675613, 0.83146961230254523708,
+                              0.70710678118654752440, 0.55557023301960222474, 0.38268343236508977173,
+                              0.19509032201612826785, 0.0};
+    const T d = T(dir);
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      C w = o[k];
+      if (k > 0) {
+        // W32^k = cos + i dir sin; for k > 8: cos(2 pi k/32) = -cos(2 pi (16-k)/32), sin = sin(2 pi (16-k)/32)
+        const int kk = k <= 8 ? k : 16 - k;
+        const ConstMul<T> cr(kc[kk]), ci(kc[8 - kk]);
+        const T sr = k <= 8 ? T(1) : T(-1);
+        const T re = sr * cr(w.x) - d * ci(w.y), im = sr * cr(w.y) + d * ci(w.x);
+        w = mk(re, im);
+      }
+      v[k] = cadd(e[k], w);
+      v[k + 16] = csub(e[k], w);
+    }
+  }
+};
+
 template <typename C> struct Dft<C, 3> {
   static __device__ __forceinline__ void run(C* v, int dir) {
     using T = typename BaseOf<C>::type;

@@ -36,6 +36,13 @@ __host__ __device__ constexpr CtPlan ct_plan(int L, int E = 8) {
     x /= 3;
     three++;
   }
+  if (E % 32 == 0 && x % 32 == 0 && x != 32 * 32) {  // one radix-32 stage, then radix 16 (512 = 32 x 16)
+    p.rad[p.nst] = 32;
+    p.ns[p.nst] = ns;
+    ns *= 32;
+    x /= 32;
+    p.nst++;
+  }
   while (E % 16 == 0 && x % 16 == 0) {
     p.rad[p.nst] = 16;
     p.ns[p.nst] = ns;

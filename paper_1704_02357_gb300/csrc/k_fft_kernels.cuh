@@ -25,6 +25,10 @@ namespace pspec {
 template <int N> struct Shape {
   static constexpr int NH = N / 2;
   static constexpr int E = elems_for(N);
+  static constexpr int EY = (N == 512) ? 32 : E;  // elements per thread in the y pass (512 = 32 x 16)
+  static constexpr int TcY = N / EY;               // threads per column in the y pass
+  static constexpr int EX = EY;                    // ... in the plain x pass
+  static constexpr int TcX = N / EX;
   static constexpr int EZ = z_elems(N);  // elements per thread in the z passes
   static constexpr int Tz = NH / EZ;     // threads per row in the z passes
   static constexpr bool ZW = Tz <= 32;   // a z row within one warp: warp-level barriers suffice
@@ -32,6 +36,7 @@ template <int N> struct Shape {
   static constexpr int TW = col_tile(N); // kz columns per tile
   static constexpr int ROWS = z_rows(N); // rows per block in the plain z passes
   static constexpr int CT = TW * Tc;     // threads of a column block
+  static constexpr int CTX = TW * TcX;   // threads of a plain x-pass block
   static constexpr int ZT = ROWS * Tz;   // threads of a row block
 };
 
@@ -262,11 +267,11 @@ __global__ void __launch_bounds__(512) k_ylm_r2c_z(const T* __restrict__ f, cx<T
 // ------------------------------------------------------------------ pass y (in place)
 // Block: one (i, kz-tile) slab, TW columns x Tc threads (column fastest).
 template <typename T, int N, int DIR, int TW>
-__global__ void __launch_bounds__(TW * Shape<N>::Tc, min_blocks<T, Shape<N>::E>(TW * Shape<N>::Tc))
+__global__ void __launch_bounds__(TW * Shape<N>::TcY, min_blocks<T, Shape<N>::EY>(TW * Shape<N>::TcY))
     k_fft_y(cx<T>* __restrict__ data, int64_t spec_stride, const ux<T>* __restrict__ twf) {
   using C = cx<T>;
   using S = Shape<N>;
-  constexpr int NH = S::NH, E = S::E, Tc = S::Tc;
+  constexpr int NH = S::NH, E = S::EY, Tc = S::TcY;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int c = threadIdx.x % TW, t = threadIdx.x / TW;
@@ -283,11 +288,11 @@ __global__ void __launch_bounds__(TW * Shape<N>::Tc, min_blocks<T, Shape<N>::E>(
 
 // ------------------------------------------------------------------ pass x (plain)
 template <typename T, int N, int DIR>
-__global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T, Shape<N>::E>(Shape<N>::CT))
+__global__ void __launch_bounds__(Shape<N>::CTX, min_blocks<T, Shape<N>::EX>(Shape<N>::CTX))
     k_fft_x(const cx<T>* in, cx<T>* out, const ux<T>* __restrict__ twf) {
   using C = cx<T>;
   using S = Shape<N>;
-  constexpr int NH = S::NH, E = S::E, Tc = S::Tc, TW = S::TW;
+  constexpr int NH = S::NH, E = S::EX, Tc = S::TcX, TW = S::TW;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int c = threadIdx.x % TW, t = threadIdx.x / TW;
@@ -605,7 +610,9 @@ template <typename T, int N> struct Passes {
   using U = ux<T>;
   using S = Shape<N>;
   static size_t smem_col() { return (size_t)N * S::TW * sizeof(C); }
-  static size_t smem_bins(int nk) { return (size_t)nk * sizeof(double) + (size_t)((S::CT + 31) / 32) * nk * sizeof(T); }
+  static size_t smem_bins(int nk, int threads = S::CT) {
+    return (size_t)nk * sizeof(double) + (size_t)((threads + 31) / 32) * nk * sizeof(T);
+  }
   static size_t smem_combine(int nk) { return smem_col() + smem_bins(nk); }
   static size_t smem_bin(int nk) { return 2 * smem_col() + smem_bins(nk); }
   // pipelined FP32 pass: two G tiles and two Y tiles (float), then the bins
@@ -661,10 +668,10 @@ template <typename T, int N> struct Passes {
     dim3 grid(N * (S::NH / TWV), nspec);
     if (dir < 0) {
       set_smem(k_fft_y<T, N, -1, TWV>, smem);
-      k_fft_y<T, N, -1, TWV><<<grid, TWV * S::Tc, smem, s>>>(data, stride, twf);
+      k_fft_y<T, N, -1, TWV><<<grid, TWV * S::TcY, smem, s>>>(data, stride, twf);
     } else {
       set_smem(k_fft_y<T, N, 1, TWV>, smem);
-      k_fft_y<T, N, 1, TWV><<<grid, TWV * S::Tc, smem, s>>>(data, stride, twf);
+      k_fft_y<T, N, 1, TWV><<<grid, TWV * S::TcY, smem, s>>>(data, stride, twf);
     }
   }
   static void fft_y(C* data, int64_t stride, int nspec, const U* twf, int dir, int variant, cudaStream_t s) {
@@ -679,10 +686,10 @@ template <typename T, int N> struct Passes {
     const unsigned grid = N * (S::NH / S::TW);
     if (dir < 0) {
       set_smem(k_fft_x<T, N, -1>, smem);
-      k_fft_x<T, N, -1><<<grid, S::CT, smem, s>>>(in, out, twf);
+      k_fft_x<T, N, -1><<<grid, S::CTX, smem, s>>>(in, out, twf);
     } else {
       set_smem(k_fft_x<T, N, 1>, smem);
-      k_fft_x<T, N, 1><<<grid, S::CT, smem, s>>>(in, out, twf);
+      k_fft_x<T, N, 1><<<grid, S::CTX, smem, s>>>(in, out, twf);
     }
   }
   static void combine_x(const C* B, C* F0, const U* twf, int interlaced, int compensate, int roundtrip,
