@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(Shape<N>::ZT, min_blocks<T, Shape<N>::EZ>(Shap
 // sequences are transformed (the staging area is reused as the exchange buffer) and
 // unpacked into the M spectra.
 template <typename T, int N, int LT>
-__global__ void __launch_bounds__(512) k_ylm_r2c_z(const T* __restrict__ f, cx<T>* __restrict__ out,
+__global__ void __launch_bounds__(ylm_thread_cap(LT), sizeof(T) == 4 ? ylm_min_blocks(LT) : 0) k_ylm_r2c_z(const T* __restrict__ f, cx<T>* __restrict__ out,
                                                   int64_t spec_stride, int ell, int h0, int M,
                                                   const ux<T>* __restrict__ twh, const ux<T>* __restrict__ twr,
                                                   const T* __restrict__ axis, int rows,

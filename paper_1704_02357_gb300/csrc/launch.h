@@ -119,6 +119,14 @@ constexpr int z_rows(int N) {
   return r;
 }
 
+// Threads of one block of the Y_lm-weighted z pass (harmonics x rows x threads per row) and
+// the resident blocks per SM its register allocation must allow (0: no requirement). The
+// unrolled l = 4 kernel launches at most 288 threads (9 x 16 x 2 at N = 512) and l = 2 at most
+// 160 (5 x 16 x 2); capping them there keeps them within 56 registers, so that 4 and 7 blocks
+// share an SM instead of 3 and 6.
+__host__ __device__ constexpr int ylm_thread_cap(int lt) { return lt == 4 ? 288 : (lt == 2 ? 160 : 512); }
+__host__ __device__ constexpr int ylm_min_blocks(int lt) { return lt == 4 ? 4 : (lt == 2 ? 7 : 0); }
+
 // Twiddle and phase tables hold ux<T> entries (FP32: {cos, sin, 1/|w| - 1, 0}); the
 // compensation table holds cx<T> {1/W_d rounded, its relative rounding error}.
 // Y_lm(khat) table of the FP32 binning pass: harmonic slots of l = 2, 4, ..., l_max in order,

@@ -17,7 +17,6 @@ constexpr size_t kAlign = 256;
 constexpr size_t kSmemBudget = 200 * 1024;   // one block
 constexpr size_t kSmemMaxBlock = 227 * 1024; // per-block limit of the device
 constexpr int kMaxElls = PSPEC_MAX_ELL / 2 + 1;
-constexpr int kYlmMaxThreads = 512;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -599,10 +598,11 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
       const int M = std::min(pl.group_max, hhi - h0);
       // z pass with the Y_lm weights: one block holds Ms harmonics x rows rows, tz threads each
       const int tz = PT->tz;
-      const int ms_max = std::max(1, std::min(c->tune.ylm_harmonics, kYlmMaxThreads / tz));
+      const int cap = ylm_thread_cap(ell);
+      const int ms_max = std::max(1, std::min(c->tune.ylm_harmonics, cap / tz));
       for (int hs = 0; hs < M; hs += ms_max) {
         const int Ms = std::min(ms_max, M - hs);
-        int rows = std::max(1, pow2_floor(std::max(1, kYlmMaxThreads / (Ms * tz))));
+        int rows = std::max(1, pow2_floor(std::max(1, cap / (Ms * tz))));
         while (rows > 1 && (((int64_t)N * N) % rows || PT->smem_ylm(Ms, rows) > kSmemBudget)) rows >>= 1;
         TRY(run(c, PSPEC_K_YLM_Z, acc(Sr + Ms * Sc), [&] {
           PT->ylm_z(f, G + hs * stride, stride, ell, h0 + hs, Ms, twh, twr, axis, rows, s);
