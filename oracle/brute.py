@@ -38,12 +38,14 @@ def _values(cat, P0, nbar_default):
 def direct_multipoles(data, randoms, params, ells: Sequence[int], k_edges) -> Dict[str, np.ndarray]:
     """Local plane-parallel estimator by explicit sums (Sec. 2.1 eq. Pell-yama).
 
-    P_l(k_b) = (2l+1)/(I N_b) sum_{k in b} Re[ A_l(k) conj(A_0(k)) ] - delta_l0 S/I with
+    P_l(k_b) = (2l+1)/(I N_b) sum_{k in b} A_l(k) conj(A_0(k)) - delta_l0 S/I with
     A_l(k) = sum_p v_p L_l(khat . rhat_p) exp(-i k . r_p) over data (v = w) and randoms
     (v = -alpha w); S/I removes the p = q pairs for l = 0. The modes are every n in
     [-N/2, N/2)^3 with no component equal to -N/2, n != 0, each counted once.
     Equals the mesh estimator when particles sit on nodes and no compensation or
-    interlacing is applied.
+    interlacing is applied. The shell sum is complex: "P" holds its real part for even l and
+    its imaginary part for odd l, "P_other" the other part (zero up to rounding, since the
+    terms at k and -k are conjugate for even l and minus conjugate for odd l).
     """
     n = params.nmesh
     L = params.box_size
@@ -77,15 +79,16 @@ def direct_multipoles(data, randoms, params, ells: Sequence[int], k_edges) -> Di
     k_mean = np.array([kmag[b == i].mean() if n_modes[i] else np.nan for i in range(nk)])
     S = np.sum(v ** 2)
     P = np.zeros((len(ells), nk))
+    other = np.zeros((len(ells), nk))
     for li, ell in enumerate(ells):
         Al = (phase * eval_legendre(ell, mu)) @ v
-        val = np.real(Al * np.conj(A0))
+        val = Al * np.conj(A0)
         for i in range(nk):
-            s = val[b == i].sum()
-            P[li, i] = (2 * ell + 1) * s / (I * n_modes[i])
+            s = (2 * ell + 1) * val[b == i].sum() / (I * n_modes[i])
+            P[li, i], other[li, i] = (s.imag, s.real) if ell % 2 else (s.real, s.imag)
             if ell == 0:
                 P[li, i] -= S / I
-    return {"P": P, "k_mean": k_mean, "n_modes": n_modes, "I": I, "S": S, "alpha": alpha}
+    return {"P": P, "P_other": other, "k_mean": k_mean, "n_modes": n_modes, "I": I, "S": S, "alpha": alpha}
 
 
 # --------------------------------------------------------------------------- Cartesian route

@@ -32,6 +32,11 @@ Conventions, and the readings of the paper they encode (each is listed in DESIGN
   P_l(k_b) = 4 pi / (I N_b) * sum_b mult * sum_m Y_lm(khat) Re[G_lm conj(F0)], l >= 2,
   with G_lm = DFT[f * Y_lm(rhat)] (Sec. 2.1 eqs. Pell-ours and Fell: the (2l+1) in front
   cancels the 4 pi/(2l+1) of the addition theorem).
+* Odd l: eq. Pell-yama's shell average of A_l(k) conj(A_0(k)) (A = sum v L_l exp(-i k.r)) is
+  purely imaginary for odd l (the terms at k and -k are complex conjugates up to the sign of
+  L_l), so P_l reports its imaginary part, 4 pi/(I N_b) sum mult sum_m Y_lm(khat)
+  Im[G_lm conj(F0)]; no shot noise. Eq. Pell-ours as printed, with F_l(-k), would flip the
+  sign of odd l; the definition followed is eq. Pell-yama, the estimator being accelerated.
 * Real spherical harmonics per eq. real-Ylm; Y_lm at the zero vector is 0 for l > 0.
 """
 from __future__ import annotations
@@ -350,8 +355,6 @@ def multipoles_from_fields(fl: Fields, params: Params, ells: Sequence[int], k_ed
     P = np.zeros((len(ells), nk))
     khat = None
     for li, ell in enumerate(ells):
-        if ell % 2:
-            raise ValueError("odd multipoles are not computed")
         if ell == 0:
             p2 = np.bincount(bs, weights=ms * np.abs(F0[sel]) ** 2, minlength=nk)
             with np.errstate(invalid="ignore", divide="ignore"):
@@ -362,7 +365,8 @@ def multipoles_from_fields(fl: Fields, params: Params, ells: Sequence[int], k_ed
         acc = np.zeros(F0.shape)
         for m in range(-ell, ell + 1):
             G = harmonic_spectrum(fl.f, params, ell, m)
-            acc += real_ylm(ell, m, *khat) * np.real(G * np.conj(F0))
+            prod = G * np.conj(F0)
+            acc += real_ylm(ell, m, *khat) * (np.imag(prod) if ell % 2 else np.real(prod))
             del G
         s = np.bincount(bs, weights=ms * acc[sel], minlength=nk)
         with np.errstate(invalid="ignore", divide="ignore"):
@@ -394,7 +398,9 @@ def lbar(ell: int, mu_lo: float, mu_hi: float) -> float:
 
 
 def wedges(P: np.ndarray, ells: Sequence[int], mu_edges) -> np.ndarray:
-    """P(k_i, mu_m) = sum_l P_l(k_i) Lbar_l(mu_m, mu_{m+1}) (Sec. 2.2 eq. wedge-est)."""
+    """P(k_i, mu_m) = sum_l P_l(k_i) Lbar_l(mu_m, mu_{m+1}) (Sec. 2.2 eq. wedge-est), even l only."""
+    if any(int(ell) % 2 for ell in ells):
+        raise ValueError("wedges are built from even multipoles")
     mu_edges = np.asarray(mu_edges, dtype=np.float64)
     nmu = len(mu_edges) - 1
     out = np.zeros((nmu, P.shape[1]))

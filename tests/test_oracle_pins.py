@@ -182,16 +182,43 @@ def _tiny_case(nmesh, seed, observer=(-37.0, -51.0, -23.0)):
 @pytest.mark.parametrize("nmesh", [8, 12, 16])
 def test_mesh_estimator_equals_direct_sum(nmesh):
     """On-node particles, CIC, no compensation/interlacing: the SH-FFT estimator equals
-    the local plane-parallel estimator summed over particles (eq. Pell-yama) exactly."""
+    the local plane-parallel estimator summed over particles (eq. Pell-yama) exactly, odd l
+    included (their imaginary part; the real part of an odd l and the imaginary part of an
+    even l vanish)."""
     d, r, p, edges = _tiny_case(nmesh, 11)
-    ells = [0, 2, 4, 6, 8]
+    ells = [0, 1, 2, 3, 4, 5, 6, 8]
     a = E.multipoles(d, r, p, ells, edges)
     b = B.direct_multipoles(d, r, p, ells, edges)
     np.testing.assert_array_equal(a["n_modes"], b["n_modes"])
     np.testing.assert_allclose(a["k_mean"], b["k_mean"], rtol=1e-13)
     scale = np.max(np.abs(b["P"][0]))
     np.testing.assert_allclose(a["P"], b["P"], rtol=1e-9, atol=1e-10 * scale)
+    assert np.max(np.abs(b["P_other"])) < 1e-10 * scale
+    # the observer sits near the box: the end-point line of sight gives odd multipoles
+    assert np.max(np.abs(b["P"][ells.index(1)])) > 1e-3 * scale
     assert abs(a["S"] - b["S"]) < 1e-12 * b["S"] and abs(a["I"] - b["I"]) < 1e-12 * b["I"]
+
+
+def test_mirror_image_keeps_every_multipole():
+    """Reflecting the catalogs and the observer through a plane maps each k shell onto itself
+    and each end-point line of sight onto its mirror, so every P_l is unchanged, odd l
+    included (pins the per-axis geometry of the moving line of sight; the sign of odd l is
+    pinned by the direct sum above)."""
+    d, r, p, edges = _tiny_case(12, 17)
+    ells = [0, 1, 2, 3]
+    a = E.multipoles(d, r, p, ells, edges)
+    # the plane through c + (N - 1) H / 2 maps node i onto node N - 1 - i
+    c = np.asarray(p.box_corner)
+    x0 = 2 * c[0] + (p.nmesh - 1) * p.cell
+    mirror = lambda x: np.column_stack([x0 - x[:, 0], x[:, 1], x[:, 2]])
+    import copy
+    d2, r2 = copy.deepcopy(d), copy.deepcopy(r)
+    d2.pos, r2.pos = mirror(d.pos), mirror(r.pos)
+    o = np.asarray(p.observer)
+    p2 = E.Params(**{**p.__dict__, "observer": (x0 - o[0], o[1], o[2])})
+    b = E.multipoles(d2, r2, p2, ells, edges)
+    scale = np.max(np.abs(a["P"][0]))
+    np.testing.assert_allclose(b["P"], a["P"], atol=1e-9 * scale)
 
 
 def _offnode_case(nmesh=16, window="tsc", interlaced=True, compensate=True, seed=5,
@@ -226,7 +253,7 @@ def test_distant_observer_limit():
     the ordinary mu-multipole (2l+1)/(I N_b) sum |F0|^2 L_l(khat_z) - delta_l0 S/I."""
     d, r, p, edges = _offnode_case(observer=(0.0, 0.0, -1e13), nmesh=16)
     fl = E.density_fields(d, r, p)
-    ells = [0, 2, 4, 6, 8]
+    ells = [0, 1, 2, 3, 4, 6, 8]
     a = E.multipoles_from_fields(fl, p, ells, edges)
     bidx, mult, n2 = E.mode_binning(p.nmesh, p.box_size, edges)
     _, _, khz = E.mode_khat(p.nmesh)
@@ -237,7 +264,8 @@ def test_distant_observer_limit():
     scale = np.max(np.abs(a["P"][0]))
     for li, ell in enumerate(ells):
         s = np.bincount(bidx[sel], weights=(mult * pw * eval_legendre(ell, khz))[sel], minlength=nk)
-        ref = (2 * ell + 1) * s / (fl.sums["I"] * nm)
+        # odd l: L_l(khat_z) |F0|^2 is odd in k, so the full shell average is 0
+        ref = (2 * ell + 1) * s / (fl.sums["I"] * nm) if ell % 2 == 0 else np.zeros(nk)
         if ell == 0:
             ref = ref - fl.sums["S"] / fl.sums["I"]
         np.testing.assert_allclose(a["P"][li], ref, atol=1e-9 * scale)

@@ -82,7 +82,8 @@ class OracleShard:
             if not q0 <= q < q1:
                 continue
             G = E.harmonic_spectrum(self.fl.f, self.p, ell, m)
-            acc = E.real_ylm(ell, m, *khat) * np.real(G * np.conj(F0))
+            prod = G * np.conj(F0)
+            acc = E.real_ylm(ell, m, *khat) * (np.imag(prod) if ell % 2 else np.real(prod))
             bins[1 + list(ells).index(ell)] += np.bincount(bs, weights=ms * acc[sel], minlength=nk)
         return self.torch.from_numpy(bins)
 
@@ -106,14 +107,14 @@ def _case():
     return p, data, randoms, edges
 
 
-def _rank_main(rank, world, port, out_dir):
+def _rank_main(rank, world, port, out_dir, ells=ELLS):
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         p, data, randoms, edges = _case()
-        res = sharded_multipoles(OracleShard(p, data, randoms), ELLS, edges)
+        res = sharded_multipoles(OracleShard(p, data, randoms), ells, edges)
         np.save(os.path.join(out_dir, f"P{rank}.npy"), res["P"])
     finally:
         dist.destroy_process_group()
@@ -125,13 +126,13 @@ def _free_port():
         return s.getsockname()[1]
 
 
-@pytest.mark.parametrize("world", [2, 3])
-def test_sharded_multipoles_over_gloo_ranks(world):
+@pytest.mark.parametrize("world,ells", [(2, ELLS), (3, ELLS), (2, [0, 1, 2, 3])])
+def test_sharded_multipoles_over_gloo_ranks(world, ells):
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
     with tempfile.TemporaryDirectory() as d:
         port = _free_port()
-        procs = [ctx.Process(target=_rank_main, args=(r, world, port, d)) for r in range(world)]
+        procs = [ctx.Process(target=_rank_main, args=(r, world, port, d, ells)) for r in range(world)]
         for pr in procs:
             pr.start()
         for pr in procs:
@@ -139,7 +140,7 @@ def test_sharded_multipoles_over_gloo_ranks(world):
         assert all(pr.exitcode == 0 for pr in procs), [pr.exitcode for pr in procs]
         Ps = [np.load(os.path.join(d, f"P{r}.npy")) for r in range(world)]
     p, data, randoms, edges = _case()
-    o = E.multipoles(data, randoms, p, ELLS, edges)
+    o = E.multipoles(data, randoms, p, ells, edges)
     scale = (np.abs(o["P"][0]) + o["S"] / o["I"]).max()
     for P in Ps:
         np.testing.assert_allclose(P, o["P"], rtol=1e-10, atol=1e-12 * scale)
