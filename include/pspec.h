@@ -78,7 +78,7 @@ typedef struct {
                               and divide each mode's binned product by prod_d sinc^{2p} (no
                               inverse transform without interlacing) */
   int32_t precision;       /* PSPEC_FP32 (FP32 meshes/transforms, FP64 sums and bins) or PSPEC_FP64 */
-  int32_t ell_max;         /* largest even l this context will be asked for, <= 16 */
+  int32_t ell_max;         /* largest l this context will be asked for, 0..16 */
   double box_size;         /* L */
   double box_corner[3];    /* position of node (0,0,0) */
   double observer[3];      /* origin of the line of sight */
@@ -137,9 +137,13 @@ pspec_status pspec_paint(void* ctx, const pspec_catalog* data, const pspec_catal
                          pspec_stats* stats);
 
 /* Steps a3-a6 on the painted meshes: P[i*n_kbins + b] for l = ells[i], k_mean[b] and
- * n_modes[b], all host arrays. `ells` (host) are even, <= the context's ell_max, any order,
- * no repeats. `k_edges` (host) has n_kbins + 1 strictly increasing, finite, >= 0 values.
- * Empty bins give NaN in P and k_mean and 0 in n_modes. */
+ * n_modes[b], all host arrays. `ells` (host) are <= the context's ell_max, any order, no
+ * repeats. `k_edges` (host) has n_kbins + 1 strictly increasing, finite, >= 0 values.
+ * Empty bins give NaN in P and k_mean and 0 in n_modes.
+ * Odd l: the shell average of eq. Pell-yama (Sec. 2.1) is purely imaginary for odd l with
+ * the end-point line of sight; P holds its imaginary part,
+ *   4 pi/(I N_b) sum_b mult sum_m Y_lm(khat) Im[G_lm conj(F0)],
+ * with Y_lm(khat) evaluated in the binning kernel (the Y table holds even l only). */
 pspec_status pspec_multipoles(void* ctx, const int32_t* ells, int32_t n_ells,
                               const double* k_edges, int32_t n_kbins,
                               double* P, double* k_mean, double* n_modes);
@@ -153,6 +157,7 @@ pspec_status pspec_multipoles_device(void* ctx, const int32_t* ells, int32_t n_e
 /* Step a7: out[w*n_kbins + b] = sum_i P[i*n_kbins + b] * Lbar_{ells[i]}(mu_w, mu_{w+1}).
  * P and out are DEVICE arrays; ells and mu_edges are host arrays; the mean Legendre
  * table is built in FP64 on the host. mu_edges: n_mu + 1 increasing values in [0, 1].
+ * ells must be even (an odd l gives PSPEC_EUNSUPPORTED).
  * Enqueued on `stream` without synchronising. */
 pspec_status pspec_wedges(const double* P, const int32_t* ells, int32_t n_ells, int32_t n_kbins,
                           const double* mu_edges, int32_t n_mu, double* out, void* stream);

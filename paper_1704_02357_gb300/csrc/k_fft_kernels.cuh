@@ -385,7 +385,10 @@ __global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T, Shape<N>::E>(Shape
 // ------------------------------------------------------------------ pass x + accumulate-and-bin
 // Per tile: F0 once (kept in shared memory, each thread its own modes); for each harmonic h
 // of the group, the x-pass of G_h and acc += Y_{l,m(h)}(khat) Re[G_h conj(F0)] per mode;
-// then mult * acc into the bins of `slot`.
+// then mult * acc into the bins of `slot`. For odd l, F0 is stored times i, so the same
+// product gives Re[G conj(i F0)] = Im[G conj(F0)].
+template <typename C> __device__ __forceinline__ C f0_for(C f, int odd) { return odd ? mk(-f.y, f.x) : f; }
+
 template <typename T, int N, bool YT>
 __global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T, Shape<N>::E>(Shape<N>::CT))
     k_bin_x(const cx<T>* G, int64_t spec_stride, int ell, int h0, int M, const cx<T>* __restrict__ F0,
@@ -417,7 +420,7 @@ __global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T, Shape<N>::E>(Shape
     T acc[E];
 #pragma unroll
     for (int e = 0; e < E; e++) {
-      sF0[(t + Tc * e) * TW + c] = F0[off + (t + Tc * e) * si];
+      sF0[(t + Tc * e) * TW + c] = f0_for(F0[off + (t + Tc * e) * si], ba.odd);
       acc[e] = T(0);
     }
     for (int s = 0; s < M; s++) {
@@ -549,7 +552,7 @@ __global__ void __launch_bounds__(Shape<N>::CT, min_blocks<float, Shape<N>::E>(S
     float acc[E];
 #pragma unroll
     for (int e = 0; e < E; e++) {
-      f0[e] = F0[off + (t + Tc * e) * si];
+      f0[e] = f0_for(F0[off + (t + Tc * e) * si], ba.odd);
       acc[e] = 0.f;
     }
     for (int s = 0; s < M; s++) {

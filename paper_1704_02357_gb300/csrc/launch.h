@@ -50,6 +50,7 @@ struct BinArgs {
   int nk;
   double* bins;              // [slots][nk] FP64 sums, added to with atomics
   const void* permode_w;     // compensation applied per mode in the binning (cx<T> per-axis table), or nullptr
+  int odd;                   // odd l: bin Y Im[G conj(F0)] instead of Y Re[G conj(F0)]
 };
 
 // a1: per-block partial sums of one weighted catalog; final combine into `derived`.

@@ -45,7 +45,7 @@ struct Plan {
   const PassTable<double>* td;
   int tw_y, tw_comb, tw_bin, rows_z;
   int group_max, ylm_rows_max;
-  int ctas_comb, ctas_bin;
+  int ctas_comb, ctas_bin, ctas_bin_plain;  // plain: the binning kernel without the Y table
   int nblk_sum;
   bool roundtrip;
   size_t Sr, Sc;
@@ -68,7 +68,7 @@ pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl,
   if (p->window != PSPEC_WINDOW_CIC && p->window != PSPEC_WINDOW_TSC) { *why = "window must be CIC or TSC"; return PSPEC_EINVAL; }
   if (p->compensate < 0 || p->compensate > 3) { *why = "compensate must be 0..3"; return PSPEC_EINVAL; }
   if (p->precision != PSPEC_FP32 && p->precision != PSPEC_FP64) { *why = "precision must be FP32 or FP64"; return PSPEC_EINVAL; }
-  if (p->ell_max < 0 || (p->ell_max & 1)) { *why = "ell_max must be even and >= 0"; return PSPEC_EUNSUPPORTED; }
+  if (p->ell_max < 0) { *why = "ell_max must be >= 0"; return PSPEC_EUNSUPPORTED; }
   if (p->ell_max > PSPEC_MAX_ELL) { *why = "ell_max > 16"; return PSPEC_EUNSUPPORTED; }
   if (!(std::isfinite(p->box_size) && p->box_size > 0)) { *why = "box_size must be finite and > 0"; return PSPEC_EINVAL; }
   for (int d = 0; d < 3; d++)
@@ -107,8 +107,9 @@ pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl,
   int m_mem = p->max_group_bytes > 0 ? (int)(p->max_group_bytes / (int64_t)pl->Sc) : nharm;
   pl->group_max = p->ell_max == 0 ? 0 : std::max(1, std::min(nharm, m_mem));
 
-  // Y_lm(khat) of every stored mode for the FP32 binning pass (l = 2..l_max)
-  pl->ytab_bytes = (size_t)N * N * NH * sizeof(float) * (size_t)ytab_base(p->ell_max + 2);
+  // Y_lm(khat) of every stored mode for the FP32 binning pass (even l = 2..l_max; odd l are
+  // binned with Y_lm evaluated in the kernel)
+  pl->ytab_bytes = (size_t)N * N * NH * sizeof(float) * (size_t)ytab_base((p->ell_max & ~1) + 2);
   pl->has_ytab = !f64 && p->ell_max >= 2 && p->ylm_table == 0 && pl->ytab_bytes <= (size_t)PSPEC_YLM_TABLE_AUTO_MAX;
   {
     size_t need = f64 ? std::max(pl->td->smem_bin(max_kbins), pl->td->smem_combine(max_kbins))
@@ -118,10 +119,11 @@ pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl,
   }
   if (f64) {
     pl->ctas_comb = pl->td->ctas(0, max_kbins, nsm);
-    pl->ctas_bin = pl->td->ctas(1, max_kbins, nsm);
+    pl->ctas_bin = pl->ctas_bin_plain = pl->td->ctas(1, max_kbins, nsm);
   } else {
     pl->ctas_comb = pl->tf->ctas(0, max_kbins, nsm);
     pl->ctas_bin = pl->tf->ctas(pl->has_ytab ? 2 : 1, max_kbins, nsm);
+    pl->ctas_bin_plain = pl->tf->ctas(1, max_kbins, nsm);
   }
   pl->nblk_sum = 2 * nsm;
 
@@ -520,6 +522,7 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
   ba.nk = nk;
   ba.bins = c->at<double>(pl.o_bins);
   ba.permode_w = c->p.compensate == 3 ? static_cast<const void*>(c->at<C>(pl.o_invw)) : nullptr;
+  ba.odd = 0;
   cudaError_t e = cudaMemsetAsync(ba.bins, 0, (size_t)(SLOT_ELL0 + std::max(n_ells, 2)) * nk * sizeof(double), s);
   if (e != cudaSuccess) return cuda_fail(c, e, "bins clear");
   int64_t transforms = 0;
@@ -529,6 +532,7 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
                                                       : pl.ctas_comb;
   const int ctas_bin = c->tune.bin_blocks_per_sm > 0 ? std::min(ntiles_x, c->tune.bin_blocks_per_sm * c->nsm)
                                                      : pl.ctas_bin;
+  const int ctas_bin_plain = c->tune.bin_blocks_per_sm > 0 ? ctas_bin : pl.ctas_bin_plain;
   auto acc = [&](double b) {
     bytes += b;
     return b;
@@ -576,7 +580,7 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
       sh += 2 * ell + 1;
       if (ell == 0) continue;
       const int nh = 2 * ell + 1;
-      const float* tb = pl.has_ytab ? c->at<float>(pl.o_ytab) + (int64_t)ytab_base(ell) * stride : nullptr;
+      const float* tb = pl.has_ytab && !(ell & 1) ? c->at<float>(pl.o_ytab) + (int64_t)ytab_base(ell) * stride : nullptr;
       jobs[njobs++] = {ell, nh, SLOT_ELL0 + i, tb};
       (void)qbase;
     }
@@ -611,8 +615,10 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
       TRY(run(c, PSPEC_K_FFT_Y, acc(2 * M * Sc), [&] { PT->fft_y(G, stride, M, twf, -1, c->tune.tile_y, s); }));
       const float* ytab = jobs[jb].table ? jobs[jb].table + (int64_t)h0 * stride : nullptr;
       const double ybytes = ytab ? M * (double)N * N * g.NH * sizeof(float) : 0.0;
+      BinArgs bj = ba;
+      bj.odd = ell > 0 && (ell & 1);
       TRY(run(c, PSPEC_K_BIN_X, acc(Sc + M * Sc + ybytes), [&] {
-        PT->bin_x(G, stride, ell, h0, M, F0, twf, jobs[jb].slot, ba, ctas_bin, ytab, s);
+        PT->bin_x(G, stride, ell, h0, M, F0, twf, jobs[jb].slot, bj, ytab ? ctas_bin : ctas_bin_plain, ytab, s);
       }));
       transforms += M;
     }
@@ -730,7 +736,6 @@ pspec_status check_ells_edges(Ctx* c, const int32_t* ells, int n_ells, const dou
   if (!ells || n_ells < 1 || n_ells > kMaxElls) { c->err = "need 1..9 multipoles"; return PSPEC_EINVAL; }
   for (int i = 0; i < n_ells; i++) {
     if (ells[i] < 0) { c->err = "negative l"; return PSPEC_EINVAL; }
-    if (ells[i] & 1) { c->err = "odd l is not computed (parity)"; return PSPEC_EUNSUPPORTED; }
     if (ells[i] > c->p.ell_max) { c->err = "l above the context's ell_max"; return PSPEC_EUNSUPPORTED; }
     for (int j = 0; j < i; j++)
       if (ells[j] == ells[i]) { c->err = "repeated l"; return PSPEC_EINVAL; }
@@ -864,7 +869,7 @@ pspec_status pspec_multipoles_cartesian(void* ctx, const int32_t* ells, int32_t 
   if (!c->pl.has_ctab) { c->err = "context created without cartesian = 1 (or not FP32)"; return PSPEC_EUNSUPPORTED; }
   TRY(check_ells_edges(c, ells, n_ells, k_edges, n_kbins));
   for (int i = 0; i < n_ells; i++)
-    if (ells[i] > 4) { c->err = "the Cartesian route covers l <= 4"; return PSPEC_EUNSUPPORTED; }
+    if (ells[i] > 4 || (ells[i] & 1)) { c->err = "the Cartesian route covers even l <= 4"; return PSPEC_EUNSUPPORTED; }
   cudaError_t e = cudaSetDevice(c->device);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
   TRY(upload_bins(c, k_edges, n_kbins));

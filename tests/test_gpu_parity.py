@@ -199,7 +199,7 @@ def test_errors_are_reported_not_faulted():
         est.multipoles([0], edges)
     assert e.value.status == pspec.ESTATE
     est.paint(d.pos, r.pos)
-    for ells, ed, st in [([3], edges, pspec.EUNSUPPORTED), ([6], edges, pspec.EUNSUPPORTED),
+    for ells, ed, st in [([5], edges, pspec.EUNSUPPORTED), ([6], edges, pspec.EUNSUPPORTED),
                          ([0, 0], edges, pspec.EINVAL), ([0], edges[::-1], pspec.EINVAL),
                          ([0], np.array([0.1]), pspec.EINVAL), ([0], np.array([0.0, np.nan]), pspec.EINVAL)]:
         with pytest.raises(PspecError) as e:
