@@ -42,3 +42,29 @@ def test_survey_512_l4_matches_oracle():
     check_fp32(g, o, ells, report=rep)
     assert rep[0]["bins_checked"] == len(edges) - 1 and rep[2]["bins_checked"] > 20 and rep[4]["bins_checked"] > 0
     print("full-size parity:", rep)
+
+
+def test_survey_512_tsc_l16_matches_golden():
+    """The l <= 16 benchmark configuration (512^3, TSC + interlacing + compensation, even l
+    up to 16, FP32) against the FP64 oracle's values stored by
+    tests/golden/make_survey512_tsc_l16.py (too slow to run here: ~150 full transforms),
+    under 1e-5 (l <= 4) and 1e-4 (l <= 16) on bins where |P_l| > 1% |P_0|."""
+    import importlib.util
+    import os
+    gold_dir = os.path.join(os.path.dirname(__file__), "golden")
+    spec = importlib.util.spec_from_file_location("make_l16", os.path.join(gold_dir, "make_survey512_tsc_l16.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    d, r, p, edges = mk.case()
+    gold = np.load(os.path.join(gold_dir, "survey512_tsc_l16.npz"))
+    assert d.size == int(gold["n_data"]) and r.size == int(gold["n_randoms"])
+    np.testing.assert_array_equal(edges, gold["edges"])
+    ells = [int(x) for x in gold["ells"]]
+    g = run_gpu(p, d, r, ells, edges, precision="fp32", max_particles=d.size + r.size)
+    np.testing.assert_array_equal(g["n_modes"], gold["n_modes"])
+    np.testing.assert_allclose(g["k_mean"], gold["k_mean"], rtol=1e-6)
+    assert abs(g["stats"]["alpha"] - float(gold["alpha"])) <= 1e-14 * float(gold["alpha"])
+    rep = {}
+    check_fp32(g, {"P": gold["P"]}, ells, report=rep)
+    assert all(rep[ell]["bins_checked"] > 100 for ell in ells)
+    print("full-size l <= 16 parity:", {ell: (v["bins_checked"], f'{v["max_rel"]:.2e}') for ell, v in rep.items()})
