@@ -265,10 +265,12 @@ __global__ void __launch_bounds__(ylm_thread_cap(LT), sizeof(T) == 4 ? ylm_min_b
 }
 
 // ------------------------------------------------------------------ pass y (in place)
-// Block: one (i, kz-tile) slab, TW columns x Tc threads (column fastest).
+// Block: one (i, kz-tile) slab, TW columns x Tc threads (column fastest). Outputs (ky, kz)
+// with ky^2 + kz^2 >= n2_cut are not stored: every mode of their x column lies beyond the
+// last bin, and the binning pass skips those columns (INT_MAX stores everything).
 template <typename T, int N, int DIR, int TW>
 __global__ void __launch_bounds__(TW * Shape<N>::TcY, min_blocks<T, Shape<N>::EY>(TW * Shape<N>::TcY))
-    k_fft_y(cx<T>* __restrict__ data, int64_t spec_stride, const ux<T>* __restrict__ twf) {
+    k_fft_y(cx<T>* __restrict__ data, int64_t spec_stride, const ux<T>* __restrict__ twf, int n2_cut) {
   using C = cx<T>;
   using S = Shape<N>;
   constexpr int NH = S::NH, E = S::EY, Tc = S::TcY;
@@ -277,13 +279,18 @@ __global__ void __launch_bounds__(TW * Shape<N>::TcY, min_blocks<T, Shape<N>::EY
   const int c = threadIdx.x % TW, t = threadIdx.x / TW;
   constexpr int ntz = NH / TW;
   const int i = blockIdx.x / ntz, kz0 = (blockIdx.x - i * ntz) * TW;
-  C* base = data + (int64_t)blockIdx.y * spec_stride + (int64_t)i * N * NH + kz0 + c;
+  if (kz0 * kz0 >= n2_cut) return;  // the whole slab is beyond the last bin (uniform per block)
+  const int kz = kz0 + c;
+  C* base = data + (int64_t)blockIdx.y * spec_stride + (int64_t)i * N * NH + kz;
   C v[E];
 #pragma unroll
   for (int e = 0; e < E; e++) v[e] = base[(int64_t)(t + Tc * e) * NH];
   fft_ct<C, E, N, kInterleaved, TW, DIR>(v, sm, t, c, twf);
 #pragma unroll
-  for (int e = 0; e < E; e++) base[(int64_t)(t + Tc * e) * NH] = v[e];
+  for (int e = 0; e < E; e++) {
+    const int ny = sfreq<N>(t + Tc * e);
+    if (ny * ny + kz * kz < n2_cut) base[(int64_t)(t + Tc * e) * NH] = v[e];
+  }
 }
 
 // ------------------------------------------------------------------ pass x (plain)
@@ -408,10 +415,11 @@ __global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T, Shape<N>::E>(Shape
   wb.init();
   const T sq2 = T(1.41421356237309504880);
   const int c = threadIdx.x % TW, t = threadIdx.x / TW;
-  constexpr int ntz = NH / TW, ntiles = N * ntz;
+  constexpr int ntz = NH / TW;
   constexpr int64_t si = (int64_t)N * NH;
   __syncthreads();
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (int q = blockIdx.x; q < ba.n_xtiles; q += gridDim.x) {
+    const int tile = ba.xtiles[q];
     const int j = tile / ntz, kz0 = (tile - j * ntz) * TW;
     const int kz = kz0 + c;
     const int64_t off = (int64_t)j * NH + kz;
@@ -524,11 +532,12 @@ __global__ void __launch_bounds__(Shape<N>::CT, min_blocks<float, Shape<N>::E>(S
   wb.w = reinterpret_cast<float*>(wb.b + ba.nk);
   wb.init();
   const int c = threadIdx.x % TW, t = threadIdx.x / TW;
-  constexpr int ntz = NH / TW, ntiles = N * ntz;
+  constexpr int ntz = NH / TW;
   constexpr int64_t si = (int64_t)N * NH;
   const float* yl = ytab;  // slot of harmonic h0; the group's slots follow
   __syncthreads();
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (int q = blockIdx.x; q < ba.n_xtiles; q += gridDim.x) {
+    const int tile = ba.xtiles[q];
     const int j = tile / ntz, kz0 = (tile - j * ntz) * TW;
     const int kz = kz0 + c;
     const int64_t off0 = (int64_t)j * NH + kz0, off = off0 + c;
@@ -666,23 +675,25 @@ template <typename T, int N> struct Passes {
     }
   }
   // variant 0: TW columns per block; variant 1: TW/2 (half the threads and shared memory)
-  template <int TWV> static void fft_y_tw(C* data, int64_t stride, int nspec, const U* twf, int dir, cudaStream_t s) {
+  template <int TWV>
+  static void fft_y_tw(C* data, int64_t stride, int nspec, const U* twf, int dir, int n2_cut, cudaStream_t s) {
     const size_t smem = (size_t)N * TWV * sizeof(C);
     dim3 grid(N * (S::NH / TWV), nspec);
     if (dir < 0) {
       set_smem(k_fft_y<T, N, -1, TWV>, smem);
-      k_fft_y<T, N, -1, TWV><<<grid, TWV * S::TcY, smem, s>>>(data, stride, twf);
+      k_fft_y<T, N, -1, TWV><<<grid, TWV * S::TcY, smem, s>>>(data, stride, twf, n2_cut);
     } else {
       set_smem(k_fft_y<T, N, 1, TWV>, smem);
-      k_fft_y<T, N, 1, TWV><<<grid, TWV * S::TcY, smem, s>>>(data, stride, twf);
+      k_fft_y<T, N, 1, TWV><<<grid, TWV * S::TcY, smem, s>>>(data, stride, twf, n2_cut);
     }
   }
-  static void fft_y(C* data, int64_t stride, int nspec, const U* twf, int dir, int variant, cudaStream_t s) {
+  static void fft_y(C* data, int64_t stride, int nspec, const U* twf, int dir, int variant, int n2_cut,
+                    cudaStream_t s) {
     constexpr int TW2 = S::TW > 1 ? S::TW / 2 : 1;
     if (variant == 1 && S::TW > 1)
-      fft_y_tw<TW2>(data, stride, nspec, twf, dir, s);
+      fft_y_tw<TW2>(data, stride, nspec, twf, dir, n2_cut, s);
     else
-      fft_y_tw<S::TW>(data, stride, nspec, twf, dir, s);
+      fft_y_tw<S::TW>(data, stride, nspec, twf, dir, n2_cut, s);
   }
   static void fft_x(const C* in, C* out, const U* twf, int dir, cudaStream_t s) {
     const size_t smem = smem_col();

@@ -51,6 +51,10 @@ struct BinArgs {
   double* bins;              // [slots][nk] FP64 sums, added to with atomics
   const void* permode_w;     // compensation applied per mode in the binning (cx<T> per-axis table), or nullptr
   int odd;                   // odd l: bin Y Im[G conj(F0)] instead of Y Re[G conj(F0)]
+  // binning pass: the x-pass tiles (j * (N/2/TW) + kz0/TW) holding a binned mode, in order
+  // (a tile whose columns all have ny^2 + kz^2 beyond the last bin is left out)
+  const int32_t* xtiles;
+  int n_xtiles;
 };
 
 // a1: per-block partial sums of one weighted catalog; final combine into `derived`.
@@ -147,7 +151,8 @@ template <typename T> struct PassTable {
   void (*c2r_z)(const cx<T>*, T*, const ux<T>*, const ux<T>*, T, cudaStream_t);
   void (*ylm_z)(const T*, cx<T>*, int64_t, int, int, int, const ux<T>*, const ux<T>*, const T*, int, cudaStream_t);
   size_t (*smem_ylm)(int, int);
-  void (*fft_y)(cx<T>*, int64_t, int, const ux<T>*, int, int, cudaStream_t);  // ..., dir, tile variant
+  // ..., dir, tile variant, n2_cut (outputs with ny^2 + kz^2 >= n2_cut are not stored)
+  void (*fft_y)(cx<T>*, int64_t, int, const ux<T>*, int, int, int, cudaStream_t);
   void (*fft_x)(const cx<T>*, cx<T>*, const ux<T>*, int, cudaStream_t);
   void (*combine_x)(const cx<T>*, cx<T>*, const ux<T>*, int, int, int, const ux<T>*, const cx<T>*, const BinArgs&,
                     int, cudaStream_t);

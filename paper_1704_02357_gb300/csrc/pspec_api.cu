@@ -1,5 +1,6 @@
 // C ABI of libpspec: plan, workspace layout, argument validation and the launch sequence
 // of the SH-FFT multipole estimator (declarations and conventions in include/pspec.h).
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -53,6 +54,7 @@ struct Plan {
   // workspace offsets
   bool has_ytab = false, has_ctab = false;
   size_t ytab_bytes = 0, o_ytab = 0, ctab_bytes = 0, o_ctab = 0;
+  size_t o_xtiles;  // x-pass tiles (j, kz-tile) of the binning pass that hold a binned mode, in order
   size_t o_mesh1, o_mesh2, o_f0, o_w, o_f, o_g, o_twh, o_twf, o_twr, o_axis, o_phase, o_invw, o_bin, o_kmag, o_cnt,
       o_lo, o_hi, o_nmodes, o_ksum, o_sums, o_derived, o_bins, o_out, o_tcnt, o_toff, o_tcur, o_prec, o_ptile,
       o_psort, total;
@@ -151,6 +153,7 @@ pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl,
   pl->ctab_bytes = pl->has_ctab ? (size_t)N * N * NH * sizeof(float) * kCartItems : 0;
   pl->o_ctab = pl->has_ctab ? take(pl->ctab_bytes) : 0;
   pl->o_bin = take((pl->n2max + 1) * sizeof(int32_t));
+  pl->o_xtiles = take((size_t)N * (NH / pl->tf->tw) * sizeof(int32_t));
   pl->o_kmag = take((pl->n2max + 1) * sizeof(double));
   pl->o_cnt = take((pl->n2max + 1) * sizeof(uint32_t));
   pl->o_lo = take(max_kbins * sizeof(int32_t));
@@ -195,6 +198,13 @@ struct Ctx {
   bool painted = false;
   bool randoms_set = false;
   std::vector<double> edges;
+  // From the bins of `edges`: no |n|^2 >= n2_cut is binned, so x columns (ny, kz) with
+  // ny^2 + kz^2 >= n2_cut are neither stored by the harmonics' y pass nor read by the binning
+  // pass. Fractions of what remains, for the byte accounting: slabs read and outputs stored
+  // by that y pass, tiles of the binning pass.
+  int n2_cut = INT_MAX;
+  int n_xtiles = 0;  // entries of the plan's x-tile list
+  double frac_yr = 1.0, frac_yw = 1.0, frac_tile = 1.0;
   // captured per-mock graph and what it was captured for
   cudaGraphExec_t graph = nullptr;
   cudaStream_t cap_stream = nullptr;  // graphs are captured and replayed here (never the legacy stream)
@@ -352,6 +362,7 @@ pspec_status upload_bins(Ctx* c, const double* edges, int nk) {
   std::vector<int32_t> bin(pl.n2max + 1), lo(nk, 0), hi(nk, 0);
   std::vector<double> kmag(pl.n2max + 1);
   const double kf = 2.0 * M_PI / c->p.box_size;
+  int n2_cut = 0;
   for (int n2 = 0; n2 <= pl.n2max; n2++) {
     const double x = (double)n2;
     int b = -1;
@@ -361,6 +372,32 @@ pspec_status upload_bins(Ctx* c, const double* edges, int nk) {
     if (b >= 0) {
       if (hi[b] == 0) lo[b] = n2;
       hi[b] = n2 + 1;
+      n2_cut = n2 + 1;
+    }
+  }
+  {
+    const int N = pl.g.N, NH = pl.g.NH;
+    const int tw = c->p.precision == PSPEC_FP64 ? pl.td->tw : pl.tf->tw;
+    const int ntz = NH / tw;
+    int64_t yr = 0, yw = 0;
+    std::vector<int32_t> xt;
+    xt.reserve((size_t)N * ntz);
+    for (int j = 0; j < N; j++) {
+      const int64_t ny2 = (int64_t)(j < NH ? j : j - N) * (j < NH ? j : j - N);
+      for (int kz = 0; kz < NH; kz++) {
+        yw += ny2 + (int64_t)kz * kz < n2_cut;
+        if (kz % tw == 0 && ny2 + (int64_t)kz * kz < n2_cut) xt.push_back(j * ntz + kz / tw);
+      }
+    }
+    for (int kz0 = 0; kz0 < NH; kz0 += tw) yr += (int64_t)kz0 * kz0 < n2_cut;
+    c->frac_yw = (double)yw / ((double)N * NH);
+    c->frac_tile = (double)xt.size() / ((double)N * ntz);
+    c->frac_yr = (double)yr / (double)ntz;
+    c->n_xtiles = (int)xt.size();
+    if (!xt.empty()) {
+      const cudaError_t ex = cudaMemcpyAsync(c->at<int32_t>(pl.o_xtiles), xt.data(), xt.size() * sizeof(int32_t),
+                                             cudaMemcpyHostToDevice, c->stream);
+      if (ex != cudaSuccess) return cuda_fail(c, ex, "tile list upload");
     }
   }
   cudaError_t er = cudaMemcpyAsync(c->at<int32_t>(pl.o_bin), bin.data(), bin.size() * sizeof(int32_t),
@@ -380,6 +417,7 @@ pspec_status upload_bins(Ctx* c, const double* edges, int nk) {
   er = cudaStreamSynchronize(c->stream);
   if (er != cudaSuccess) return cuda_fail(c, er, "bin table upload");
   c->edges = e;
+  c->n2_cut = n2_cut;
   return PSPEC_OK;
 }
 
@@ -523,6 +561,8 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
   ba.bins = c->at<double>(pl.o_bins);
   ba.permode_w = c->p.compensate == 3 ? static_cast<const void*>(c->at<C>(pl.o_invw)) : nullptr;
   ba.odd = 0;
+  ba.xtiles = c->at<int32_t>(pl.o_xtiles);
+  ba.n_xtiles = c->n_xtiles;
   cudaError_t e = cudaMemsetAsync(ba.bins, 0, (size_t)(SLOT_ELL0 + std::max(n_ells, 2)) * nk * sizeof(double), s);
   if (e != cudaSuccess) return cuda_fail(c, e, "bins clear");
   int64_t transforms = 0;
@@ -540,12 +580,12 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
 
   // a3: F1 (and F2), combine + compensate -> F0 with the l = 0 sums; round trip -> f
   TRY(run(c, PSPEC_K_FFT_Z, acc(Sr + Sc), [&] { PT->r2c_z(m1, F0, twh, twr, s); }));
-  TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { PT->fft_y(F0, 0, 1, twf, -1, c->tune.tile_y, s); }));
+  TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { PT->fft_y(F0, 0, 1, twf, -1, c->tune.tile_y, INT_MAX, s); }));
   transforms++;
   if (c->p.interlaced) {
     TRY(run(c, PSPEC_K_FFT_X, acc(2 * Sc), [&] { PT->fft_x(F0, F0, twf, -1, s); }));
     TRY(run(c, PSPEC_K_FFT_Z, acc(Sr + Sc), [&] { PT->r2c_z(m2, W, twh, twr, s); }));
-    TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { PT->fft_y(W, 0, 1, twf, -1, c->tune.tile_y, s); }));
+    TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { PT->fft_y(W, 0, 1, twf, -1, c->tune.tile_y, INT_MAX, s); }));
     transforms++;
     TRY(run(c, PSPEC_K_COMBINE, acc(3 * Sc), [&] {
       PT->combine_x(W, F0, twf, 1, c->p.compensate, pl.roundtrip, phase, invw, ba, ctas_comb, s);
@@ -557,7 +597,7 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
   }
   if (pl.roundtrip) {
     TRY(run(c, PSPEC_K_FFT_X, acc(2 * Sc), [&] { PT->fft_x(F0, W, twf, +1, s); }));
-    TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { PT->fft_y(W, 0, 1, twf, +1, c->tune.tile_y, s); }));
+    TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { PT->fft_y(W, 0, 1, twf, +1, c->tune.tile_y, INT_MAX, s); }));
     const T scale = T(2.0 / ((double)N * N * N));
     TRY(run(c, PSPEC_K_C2R_Z, acc(Sc + Sr), [&] { PT->c2r_z(W, f, twh, twr, scale, s); }));
     transforms++;
@@ -612,12 +652,13 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
           PT->ylm_z(f, G + hs * stride, stride, ell, h0 + hs, Ms, twh, twr, axis, rows, s);
         }));
       }
-      TRY(run(c, PSPEC_K_FFT_Y, acc(2 * M * Sc), [&] { PT->fft_y(G, stride, M, twf, -1, c->tune.tile_y, s); }));
+      TRY(run(c, PSPEC_K_FFT_Y, acc(M * Sc * (c->frac_yr + c->frac_yw)),
+              [&] { PT->fft_y(G, stride, M, twf, -1, c->tune.tile_y, c->n2_cut, s); }));
       const float* ytab = jobs[jb].table ? jobs[jb].table + (int64_t)h0 * stride : nullptr;
       const double ybytes = ytab ? M * (double)N * N * g.NH * sizeof(float) : 0.0;
       BinArgs bj = ba;
       bj.odd = ell > 0 && (ell & 1);
-      TRY(run(c, PSPEC_K_BIN_X, acc(Sc + M * Sc + ybytes), [&] {
+      TRY(run(c, PSPEC_K_BIN_X, acc((Sc + M * Sc + ybytes) * c->frac_tile), [&] {
         PT->bin_x(G, stride, ell, h0, M, F0, twf, jobs[jb].slot, bj, ytab ? ctas_bin : ctas_bin_plain, ytab, s);
       }));
       transforms += M;

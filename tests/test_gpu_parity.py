@@ -345,3 +345,27 @@ def test_compensation_forms_match_oracle(form, precision, nmesh, window, interla
     o_sinc = E.multipoles(d, r, replace(p, compensation="sinc"), ells, edges)
     k = 0 if form == "jing" else 1  # per mode, l = 0 is identical by construction
     assert np.max(np.abs(o_sinc["P"][k] - o["P"][k]) / scale) > 1e-4
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_columns_beyond_the_last_bin_are_skipped_exactly(precision):
+    """Bins ending well below k_N: the harmonics' y pass stores, and the binning pass reads,
+    only x columns (ky, kz) that hold a binned mode (whole y-pass slabs drop out here). The
+    result equals the oracle's, also when the same context alternates low and full edges."""
+    d, r, p, _ = _offnode(64, "tsc", True, True, seed=31)
+    ells = [0, 1, 2, 4]
+    low = np.linspace(0.0, 0.3 * math.pi * 64 / p.box_size, 6)
+    full = np.linspace(0.0, math.pi * 64 / p.box_size * math.sqrt(3.0), 7)
+    est = gpu_estimator(p, precision=precision, ell_max=4)
+    est.paint(d.pos, r.pos)
+    for edges in (low, full, low):
+        g = est.multipoles(ells, edges)
+        o = E.multipoles(d, r, p, ells, edges)
+        np.testing.assert_array_equal(g["n_modes"], o["n_modes"])
+        fin = o["n_modes"] > 0
+        scale = (np.abs(o["P"][0]) + o["S"] / o["I"])[fin]
+        if precision == "fp64":
+            np.testing.assert_allclose(g["P"][:, fin], o["P"][:, fin], rtol=1e-8, atol=1e-10 * scale.max())
+        else:
+            check_fp32({"P": g["P"][:, fin]}, {"P": o["P"][:, fin]}, ells, scale=scale)
+    est.close()
