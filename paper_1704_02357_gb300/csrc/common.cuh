@@ -233,8 +233,9 @@ template <typename T> struct YTab {
   T Bl[kLdim * kLdim];
 };
 
-// HILO = false: coefficients rounded to T only (the real-space weights Y_lm(rhat), whose
-// smooth errors only rescale the k-independent noise term and do not leak; measured).
+// HILO = false: coefficients rounded to T only. Both spaces use HILO = true: a coherent error
+// in the real-space weights Y_lm(rhat) leaks part of the shot noise into P_l through shell sums
+// of Y_lm(khat) that the mesh's cubic symmetry leaves nonzero, and it grows with l.
 template <typename T, bool HILO = true>
 __device__ __forceinline__ T ylm_q(const YTab<T>& t, int ell, int a, T z) {
   T q2 = t.c[a];
@@ -313,10 +314,6 @@ template <> __device__ __forceinline__ float rsqrt_t<float>(float x) {
   return fmaf(0.5f * y, e, y);
 }
 template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return 1.0 / sqrt(x); }
-// The plain hardware approximation (FP32), for the real-space directions rhat.
-template <typename T> __device__ __forceinline__ T rsqrt_fast(T x) {
-  if constexpr (sizeof(T) == 4) return rsqrtf(x);
-  else return 1.0 / sqrt(x);
-}
+
 
 }  // namespace pspec

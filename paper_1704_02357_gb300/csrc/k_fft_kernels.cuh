@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(ylm_thread_cap(LT), sizeof(T) == 4 ? ylm_min_b
         }
         continue;
       }
-      const T inv = rsqrt_fast<T>(r2);
+      const T inv = rsqrt_t<T>(r2);
       const T x = vx * inv, y = vy * inv, z = vz * inv;
       T pr = T(1), pi = T(0);
       if constexpr (LT > 0) {
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(ylm_thread_cap(LT), sizeof(T) == 4 ? ylm_min_b
 #pragma unroll
         for (int a = 0; a <= LT; a++) {
           if (a >= a_lo && a <= a_hi) {
-            const T q = fv * ylm_q<T, false>(yt, LT, a, z);
+            const T q = fv * ylm_q<T, true>(yt, LT, a, z);
             if (a == 0) {
               stage[r * N + kk] = q;
             } else {
@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(ylm_thread_cap(LT), sizeof(T) == 4 ? ylm_min_b
           pr = nr;
         }
         for (int a = a_lo; a <= a_hi; a++) {
-          const T q = fv * ylm_q<T, false>(yt, ell, a, z);
+          const T q = fv * ylm_q<T, true>(yt, ell, a, z);
           if (a == 0) {
             stage[r * N + kk] = q;
           } else {
