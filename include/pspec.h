@@ -139,7 +139,9 @@ pspec_status pspec_paint(void* ctx, const pspec_catalog* data, const pspec_catal
 /* Steps a3-a6 on the painted meshes: P[i*n_kbins + b] for l = ells[i], k_mean[b] and
  * n_modes[b], all host arrays. `ells` (host) are <= the context's ell_max, any order, no
  * repeats. `k_edges` (host) has n_kbins + 1 strictly increasing, finite, >= 0 values.
- * Empty bins give NaN in P and k_mean and 0 in n_modes.
+ * Empty bins give NaN in P and k_mean and 0 in n_modes. Modes at or beyond the last edge are
+ * never binned, and the harmonics' transforms skip x columns made only of such modes, so the
+ * cost falls when the edges stop below the largest |k| of the mesh.
  * Odd l: the shell average of eq. Pell-yama (Sec. 2.1) is purely imaginary for odd l with
  * the end-point line of sight; P holds its imaginary part,
  *   4 pi/(I N_b) sum_b mult sum_m Y_lm(khat) Im[G_lm conj(F0)],
