@@ -359,6 +359,11 @@ def test_lbar_closed_form_vs_quadrature():
             assert abs(E.lbar(ell, lo, hi) - q) < 1e-12
 
 
+def test_wedges_refuse_odd_multipoles():
+    with pytest.raises(ValueError):
+        E.wedges(np.ones((2, 3)), [0, 1], [0.0, 0.5, 1.0])
+
+
 def test_wedge_sum_rule_and_pure_multipole():
     rng = np.random.default_rng(0)
     ells = list(range(0, 17, 2))

@@ -54,6 +54,9 @@ def test_harmonic_items_order_and_count():
     # every (l, m) once; with the one l = 0 transform this is the SH transform count
     assert len(set(items)) == len(items)
     assert len(harmonic_items(range(0, 9, 2))) + 1 == E.fft_count_sh(8)
+    # odd l: 2l+1 harmonics each, in the order asked
+    odd = harmonic_items([3, 0, 1])
+    assert len(odd) == 7 + 3 and odd[:3] == [(3, 0), (3, 1), (3, -1)] and odd[-3:] == [(1, 0), (1, 1), (1, -1)]
 
 
 class OracleShard:
