@@ -5,7 +5,7 @@ against the paper by eye: no blocking, fusion or reordering beyond what the pape
 Library primitives used as steps: ``numpy.fft``/``scipy.fft`` (r2c and c2r DFTs),
 ``scipy.special.lpmv`` (associated Legendre functions), ``scipy.special.eval_legendre``.
 
-Conventions, and the readings of the paper they encode (each is listed in the design doc):
+Conventions, and the readings of the paper they encode:
 
 * Mesh: N^3 nodes at x_i = corner + i*H, H = L/N, index order (x, y, z), z fastest.
 * Forward DFT with exp(-i k.x), unnormalised; integer frequencies n in [-N/2, N/2).
