@@ -31,7 +31,7 @@ def tol_for(ell):
 
 
 def check_fp32(gpu, ora, ells, scale=None, report=None):
-    """North-star rule: |dP_l| / |P_l| <= tol(l) in bins where |P_l| > 1% |P_0|.
+    """Tolerance rule: |dP_l| / |P_l| <= tol(l) in bins where |P_l| > 1% |P_0|.
 
     ``scale`` replaces |P_0| as the reference amplitude when the monopole carries no
     signal (uniform Poisson points: P_0 ~ 0); the rule is then |dP_l| <= tol(l) * scale.

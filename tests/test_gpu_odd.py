@@ -83,7 +83,7 @@ def test_odd_with_and_without_the_ylm_table():
 
 def test_survey_shaped_dipole_fp32():
     """A survey cap seen from the observer at the origin: the wide-angle dipole and octupole
-    of the end-point line of sight, FP32, under the spec rule on the bins where
+    of the end-point line of sight, FP32, under the tolerance rule on the bins where
     |P_l| > 1% |P_0|."""
     geo = synth.survey_geometry()
     fld = synth.lognormal_field(64, geo.box_size, geo.box_corner, seed=3)

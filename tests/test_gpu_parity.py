@@ -118,7 +118,7 @@ def test_config_plain_box_64():
 
 def test_survey_shaped_high_ell_fp32():
     """A survey cap (lognormal, redshift-space, TSC + interlacing) at l <= 16, FP32, with
-    the benchmark spec's tolerances on bins where |P_l| > 1% |P_0|."""
+    the stated tolerances on bins where |P_l| > 1% |P_0|."""
     geo = synth.survey_geometry()
     fld = synth.lognormal_field(64, geo.box_size, geo.box_corner, seed=3)
     d = synth.survey_catalog(fld, geo, nbar=1e-4, seed=33)
