@@ -1,8 +1,11 @@
-"""Full-size parity: the survey workload of the benchmark (512^3, CIC + interlacing,
-l = 0, 2, 4, FP32) against the FP64 oracle, bin by bin, under the stated tolerances.
+"""The survey workloads against the FP64 oracle, bin by bin, under the stated tolerances: a 96^3
+survey cap at l <= 16, and at full size the benchmark's 512^3 workload (CIC + interlacing,
+l = 0, 2, 4, FP32) and its l <= 16 TSC configuration.
 
-Higher multipoles (l <= 16) are checked against the oracle at 96^3 in test_gpu_parity.py;
-at 512^3 the oracle would need ~150 full transforms and Y_lm evaluations (tens of minutes).
+At 512^3 the l <= 16 check uses the oracle's stored values (recomputing them would need ~150
+full transforms and Y_lm evaluations, over an hour). The worst bins here sit close to the FP32
+rounding floor of the transforms, so this file is collected after every other GPU test: a run
+stopping at the first failure has run the rest.
 """
 import math
 
@@ -11,7 +14,7 @@ import pytest
 
 import synth
 from oracle import estimator as E
-from tests._parity import check_fp32, run_gpu
+from tests._parity import check_fp32, run_gpu, uniform_edges
 
 pytestmark = pytest.mark.gpu
 
@@ -20,6 +23,26 @@ pytestmark = pytest.mark.gpu
 def _built():
     from paper_1704_02357_gb300 import build
     build.build()
+
+
+def test_survey_shaped_high_ell_fp32():
+    """A survey cap (lognormal, redshift-space, TSC + interlacing) at l <= 16, FP32, with
+    the stated tolerances on bins where |P_l| > 1% |P_0|."""
+    geo = synth.survey_geometry()
+    fld = synth.lognormal_field(64, geo.box_size, geo.box_corner, seed=3)
+    d = synth.survey_catalog(fld, geo, nbar=1e-4, seed=33)
+    r = synth.survey_randoms(5 * d.size, geo, seed=4)
+    r.nbar = np.full(r.size, 1e-4)
+    p = E.Params(nmesh=96, box_size=geo.box_size, box_corner=tuple(geo.box_corner), window="tsc",
+                 interlaced=True, compensate=True, P0=1e4, nbar=1e-4)
+    edges = uniform_edges(0.005, 0.145, 0.01)
+    ells = list(range(0, 17, 2))
+    o = E.multipoles(d, r, p, ells, edges)
+    g = run_gpu(p, d, r, ells, edges, precision="fp32")
+    rep = {}
+    check_fp32(g, o, ells, report=rep)
+    assert rep[0]["bins_checked"] == len(edges) - 1
+    assert rep[2]["bins_checked"] > 0 and rep[4]["bins_checked"] > 0
 
 
 def test_survey_512_l4_matches_oracle():
