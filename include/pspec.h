@@ -245,9 +245,12 @@ pspec_status pspec_run_batch(void* ctx, const pspec_catalog* mocks, int32_t n_mo
  * until the process exits; `nblocks` partial sums per catalog (0 = twice the SM count, at
  * most PSPEC_NOALLOC_MAX_BLOCKS; a larger value gives PSPEC_EINVAL). The first call on a
  * device looks up that array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture. Every call on a device shares
- * the array, so calls that overlap on the GPU (different streams, no ordering) race. The
- * call is enqueued on `stream` and does not synchronise. */
+ * current; make that first call before any stream capture. The address is kept for the
+ * life of the process, so a device that cudaDeviceReset has reset must not be used with this
+ * call again. Every call on a device shares the array, so calls that overlap on the GPU
+ * (different streams, no ordering) race. The call is enqueued on `stream` and does not
+ * synchronise. A CUDA error already pending on the calling thread gives PSPEC_ECUDA before
+ * anything is launched (the error is left pending for its owner). */
 #define PSPEC_NOALLOC_MAX_BLOCKS 1024
 pspec_status pspec_catalog_sums_noalloc(const pspec_params* p, const pspec_catalog* data,
                                         const pspec_catalog* randoms, int32_t nblocks, double* out,

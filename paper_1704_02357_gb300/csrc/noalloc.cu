@@ -25,7 +25,10 @@ std::mutex g_mu;
 double* g_scratch_addr[kMaxDevices] = {};
 
 // The device address of g_sums_scratch on the current device. In host code the symbol is
-// only a host-side stand-in, so the address is looked up once per device and cached.
+// only a host-side stand-in, so the address is looked up once per device (the first call on a
+// device, with that device current) and cached. cudaDeviceReset destroys the context the
+// address belongs to: a process that resets a device must not call this entry point on it
+// again.
 pspec_status scratch_on_current_device(double** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PSPEC_ECUDA;
@@ -71,6 +74,9 @@ extern "C" pspec_status pspec_catalog_sums_noalloc(const pspec_params* p, const 
   if (!p || !out || !catalog_ok(data, false) || !catalog_ok(randoms, true)) return PSPEC_EINVAL;
   if (!(p->box_size > 0) || p->nmesh < 1) return PSPEC_EINVAL;
   if (nblocks < 0 || nblocks > PSPEC_NOALLOC_MAX_BLOCKS) return PSPEC_EINVAL;
+  // An error already pending on this thread is the caller's: report it without launching and
+  // leave it in place, so that the status below belongs to this call's launches alone.
+  if (cudaPeekAtLastError() != cudaSuccess) return PSPEC_ECUDA;
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return PSPEC_ECUDA;
@@ -83,7 +89,9 @@ extern "C" pspec_status pspec_catalog_sums_noalloc(const pspec_params* p, const 
   double* part_r = scratch + (size_t)PSPEC_NOALLOC_MAX_BLOCKS * kSumVals;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   launch_catalog_partials(args_for(p, data), part_d, nblocks, s);
+  if (cudaGetLastError() != cudaSuccess) return PSPEC_ECUDA;
   launch_catalog_partials(args_for(p, randoms), part_r, nblocks, s);
+  if (cudaGetLastError() != cudaSuccess) return PSPEC_ECUDA;
   launch_catalog_final(part_d, nblocks, part_r, nblocks, out, s);
   return cudaGetLastError() == cudaSuccess ? PSPEC_OK : PSPEC_ECUDA;
 }

@@ -407,15 +407,49 @@ def wedges(P, ells: Sequence[int], mu_edges, stream=None):
 
 def catalog_sums_noalloc(params: Params, data_pos, randoms_pos, out, data_weight=None, data_nbar=None,
                          randoms_weight=None, randoms_nbar=None, nblocks=0, stream=None):
-    """Enqueue pspec_catalog_sums_noalloc: `out` is a float64 CUDA tensor of >= 10 elements."""
+    """Enqueue pspec_catalog_sums_noalloc (the catalog sums of paint, without device allocation).
+
+    Every array must already be a contiguous CUDA tensor on `out`'s device: positions float64
+    or float32 (n, 3), weights and nbar float64. Nothing is copied or converted here, so the
+    call allocates no device memory (a host array or a tensor on another device raises
+    ValueError instead of being copied over). `out` is a contiguous float64 CUDA tensor of at
+    least 10 elements; it receives the values in the order of the library's derived layout
+    (W_d, W_r, alpha, I, S, ...). The call is enqueued on `stream` (default: the current stream
+    of `out`'s device) with that device current.
+    """
     import torch
+    if not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.float64
+            and out.is_contiguous() and out.numel() >= 10):
+        raise ValueError("out must be a contiguous float64 CUDA tensor of at least 10 elements")
+
+    def dev_array(a, name, dtypes, ndim):
+        if a is None:
+            return None
+        if not (isinstance(a, torch.Tensor) and a.is_cuda and a.device == out.device and a.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous CUDA tensor on {out.device} (no copies are made)")
+        if a.dtype not in dtypes or a.dim() != ndim or (ndim == 2 and a.shape[1] != 3):
+            raise ValueError(f"{name} has dtype {a.dtype} and shape {tuple(a.shape)}")
+        return a
+
+    pos_t = (torch.float64, torch.float32)
+    f64 = (torch.float64,)
+    dp = dev_array(data_pos, "data_pos", pos_t, 2)
+    rp = dev_array(randoms_pos, "randoms_pos", pos_t, 2)
+    if dp is None or rp is None:
+        raise ValueError("data_pos and randoms_pos are required")
+    dw, dn = dev_array(data_weight, "data_weight", f64, 1), dev_array(data_nbar, "data_nbar", f64, 1)
+    rw, rn = dev_array(randoms_weight, "randoms_weight", f64, 1), dev_array(randoms_nbar, "randoms_nbar", f64, 1)
+    for a, n in ((dw, dp), (dn, dp), (rw, rp), (rn, rp)):
+        if a is not None and a.shape[0] != n.shape[0]:
+            raise ValueError("a weight or nbar array does not match its positions")
     lib = load()
-    keep = []
-    d = _catalog(data_pos, data_weight, data_nbar, out.device, keep)
-    r = _catalog(randoms_pos, randoms_weight, randoms_nbar, out.device, keep)
-    s = stream if stream is not None else torch.cuda.current_stream(out.device)
-    st = lib.pspec_catalog_sums_noalloc(C.byref(params), C.byref(d), C.byref(r), int(nblocks),
-                                        C.c_void_p(out.data_ptr()), C.c_void_p(s.cuda_stream))
+    with torch.cuda.device(out.device):
+        keep = []
+        d = _catalog(dp, dw, dn, out.device, keep)
+        r = _catalog(rp, rw, rn, out.device, keep)
+        s = stream if stream is not None else torch.cuda.current_stream(out.device)
+        st = lib.pspec_catalog_sums_noalloc(C.byref(params), C.byref(d), C.byref(r), int(nblocks),
+                                            C.c_void_p(out.data_ptr()), C.c_void_p(s.cuda_stream))
     _check(st)
     return keep
 

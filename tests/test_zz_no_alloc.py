@@ -69,3 +69,24 @@ def test_noalloc_rejects_more_partials_than_its_scratch_holds():
     ref = est.paint(dp, rp, dw, dn, rw, rn)
     assert abs(out[2].item() - ref["alpha"]) <= 1e-12 * ref["alpha"]
     est.close()
+
+
+def test_noalloc_binding_checks_its_buffers_instead_of_copying():
+    """The Python binding refuses what would make it allocate or write out of bounds: a short
+    or non-float64 `out`, and catalog arrays that are not already contiguous tensors on `out`'s
+    device (it would otherwise have to copy them there)."""
+    import torch
+    from paper_1704_02357_gb300 import Estimator, pspec
+    dev = torch.device("cuda", 0)
+    est = Estimator(nmesh=32, box_size=400.0, box_corner=(0.0, 0.0, 0.0), P0=1e4, nbar=1e-4, device=dev)
+    dp, rp, dw, dn, rw, rn = _catalogs(4, dev)
+    for bad in (torch.zeros(9, dtype=torch.float64, device=dev), torch.zeros(10, dtype=torch.float32, device=dev),
+                torch.zeros(10, dtype=torch.float64)):
+        with pytest.raises(ValueError):
+            pspec.catalog_sums_noalloc(est.params, dp, rp, bad, dw, dn, rw, rn)
+    out = torch.zeros(10, dtype=torch.float64, device=dev)
+    with pytest.raises(ValueError):
+        pspec.catalog_sums_noalloc(est.params, dp.cpu().numpy(), rp, out)
+    with pytest.raises(ValueError):
+        pspec.catalog_sums_noalloc(est.params, dp, rp, out, dw[:-1])
+    est.close()
