@@ -18,6 +18,7 @@
 #include <cmath>
 #include "launch.h"
 #include "fft_engine.cuh"
+#include "xp_engine.cuh"
 
 namespace pspec {
 
@@ -29,6 +30,10 @@ template <int N> struct Shape {
   static constexpr int TcY = N / EY;               // threads per column in the y pass
   static constexpr int EX = EY;                    // ... in the plain x pass
   static constexpr int TcX = N / EX;
+  // Exact-add y and plain x passes (FP32): no radix-32 stage (its 32 pairs h + l would not fit
+  // in registers), 512 = 16 x 16 x 2 with 16 elements per thread.
+  static constexpr int EYX = (N == 512) ? 16 : E;
+  static constexpr int TcYX = N / EYX;
   static constexpr int EZ = z_elems(N);  // elements per thread in the z passes
   static constexpr int Tz = NH / EZ;     // threads per row in the z passes
   static constexpr bool ZW = Tz <= 32;   // a z row within one warp: warp-level barriers suffice
@@ -38,6 +43,18 @@ template <int N> struct Shape {
   static constexpr int CT = TW * Tc;     // threads of a column block
   static constexpr int CTX = TW * TcX;   // threads of a plain x-pass block
   static constexpr int ZT = ROWS * Tz;   // threads of a row block
+};
+
+// Row shapes of the z passes: the plain ones (Shape), or for exact-add stages (XP) at most 8
+// elements per thread (16 pairs h + l would not fit in registers at the occupancy these passes
+// need), the same threads per block.
+template <int N, bool XP> struct ZShape {
+  using S = Shape<N>;
+  static constexpr int E = (XP && S::EZ == 16) ? 8 : S::EZ;
+  static constexpr int Tz = S::NH / E;
+  static constexpr bool ZW = Tz <= 32;
+  static constexpr int ROWS = (S::ROWS * S::Tz / Tz) > 0 ? (S::ROWS * S::Tz / Tz) : 1;
+  static constexpr int ZT = ROWS * Tz;
 };
 
 // Resident blocks per SM the register allocation must allow. Threads holding 24 complex
@@ -125,13 +142,14 @@ __global__ void __launch_bounds__(Shape<N>::ZT, min_blocks<T, Shape<N>::EZ>(Shap
 
 // ------------------------------------------------------------------ pass z: c2r
 // Rows of L stored modes (the kz = N/2 mode taken as 0) -> N reals, times `scale`.
-template <typename T, int N>
-__global__ void __launch_bounds__(Shape<N>::ZT, min_blocks<T, Shape<N>::EZ>(Shape<N>::ZT))
+// XP: exact-add pack and stages (FP32 only).
+template <typename T, int N, bool XP>
+__global__ void __launch_bounds__(ZShape<N, XP>::ZT, min_blocks<T, ZShape<N, XP>::E>(ZShape<N, XP>::ZT))
     k_c2r_z(const cx<T>* __restrict__ in, T* __restrict__ out, const ux<T>* __restrict__ twh,
             const ux<T>* __restrict__ twr, T scale) {
   using C = cx<T>;
-  using S = Shape<N>;
-  constexpr int L = S::NH, E = S::EZ, Tc = S::Tz;
+  using S = ZShape<N, XP>;
+  constexpr int L = N / 2, E = S::E, Tc = S::Tz;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int r = threadIdx.x / Tc, t = threadIdx.x - r * Tc;
@@ -142,12 +160,16 @@ __global__ void __launch_bounds__(Shape<N>::ZT, min_blocks<T, Shape<N>::EZ>(Shap
   for (int e = 0; e < E; e++) {
     const int k = t + Tc * e;
     const C xk = src[k];
-    const C xm = k ? cconj(src[L - k]) : mk(T(0), T(0));
-    const C ev = cscale(cadd(xk, xm), T(0.5));
-    const C od = umul(cscale(csub(xk, xm), T(0.5)), uconj(ldg_u(twr + k)));
-    v[e] = mk(ev.x - od.y, ev.y + od.x);  // E + i O
+    if constexpr (XP) {
+      v[e] = c2r_pack_xp(xk, k ? src[L - k] : mk(T(0), T(0)), uconj(ldg_u(twr + k)));
+    } else {
+      const C xm = k ? cconj(src[L - k]) : mk(T(0), T(0));
+      const C ev = cscale(cadd(xk, xm), T(0.5));
+      const C od = umul(cscale(csub(xk, xm), T(0.5)), uconj(ldg_u(twr + k)));
+      v[e] = mk(ev.x - od.y, ev.y + od.x);  // E + i O
+    }
   }
-  fft_ct<C, E, L, kPaddedRows, 1, +1, S::ZW>(v, sm, t, r, twh);
+  fft_any<XP, C, E, L, kPaddedRows, 1, +1, S::ZW>(v, sm, t, r, twh);
   C* dst = reinterpret_cast<C*>(out + (int64_t)row * N);
 #pragma unroll
   for (int e = 0; e < E; e++) dst[t + Tc * e] = cscale(v[e], scale);
@@ -159,15 +181,15 @@ __global__ void __launch_bounds__(Shape<N>::ZT, min_blocks<T, Shape<N>::EZ>(Shap
 // area of nseq = M*rows real rows; then each of the nseq*Tz threads loads its slots, the
 // sequences are transformed (the staging area is reused as the exchange buffer) and
 // unpacked into the M spectra.
-template <typename T, int N, int LT>
-__global__ void __launch_bounds__(ylm_thread_cap(LT), sizeof(T) == 4 ? ylm_min_blocks(LT) : 0) k_ylm_r2c_z(const T* __restrict__ f, cx<T>* __restrict__ out,
+template <typename T, int N, int LT, bool XP>
+__global__ void __launch_bounds__(ylm_thread_cap(LT), sizeof(T) == 4 ? ylm_min_blocks(LT, XP) : 0) k_ylm_r2c_z(const T* __restrict__ f, cx<T>* __restrict__ out,
                                                   int64_t spec_stride, int ell, int h0, int M,
                                                   const ux<T>* __restrict__ twh, const ux<T>* __restrict__ twr,
                                                   const T* __restrict__ axis, int rows,
                                                   const __grid_constant__ YTab<T> yt) {
   using C = cx<T>;
-  using S = Shape<N>;
-  constexpr int L = S::NH, E = S::EZ, Tc = S::Tz;
+  using S = ZShape<N, XP>;
+  constexpr int L = N / 2, E = S::E, Tc = S::Tz;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* stage = reinterpret_cast<T*>(smraw);  // [nseq][N] reals, then the exchange buffer
   C* xb = reinterpret_cast<C*>(smraw);
@@ -249,7 +271,7 @@ __global__ void __launch_bounds__(ylm_thread_cap(LT), sizeof(T) == 4 ? ylm_min_b
 #pragma unroll
   for (int e = 0; e < E; e++) v[e] = stc[sq * L + t + Tc * e];
   __syncthreads();
-  fft_ct<C, E, L, kPaddedRows, 1, -1, S::ZW>(v, xb, t, sq, twh);
+  fft_any<XP, C, E, L, kPaddedRows, 1, -1, S::ZW>(v, xb, t, sq, twh);
   // mirrors through shared memory (shuffles would raise this kernel's register count, measured slower)
 #pragma unroll
   for (int e = 0; e < E; e++) xb[sidx<kPaddedRows, L, 1>(sq, t + Tc * e)] = v[e];
@@ -260,7 +282,10 @@ __global__ void __launch_bounds__(ylm_thread_cap(LT), sizeof(T) == 4 ? ylm_min_b
   for (int e = 0; e < E; e++) {
     const int k = t + Tc * e;
     const C zm = xb[sidx<kPaddedRows, L, 1>(sq, k ? L - k : 0)];
-    dst[k] = r2c_unpack<C, T>(v[e], zm, ldg_u(twr + k));
+    if constexpr (XP)
+      dst[k] = r2c_unpack_xp(v[e], zm, ldg_u(twr + k));
+    else
+      dst[k] = r2c_unpack<C, T>(v[e], zm, ldg_u(twr + k));
   }
 }
 
@@ -268,12 +293,15 @@ __global__ void __launch_bounds__(ylm_thread_cap(LT), sizeof(T) == 4 ? ylm_min_b
 // Block: one (i, kz-tile) slab, TW columns x Tc threads (column fastest). Outputs (ky, kz)
 // with ky^2 + kz^2 >= n2_cut are not stored: every mode of their x column lies beyond the
 // last bin, and the binning pass skips those columns (INT_MAX stores everything).
-template <typename T, int N, int DIR, int TW>
-__global__ void __launch_bounds__(TW * Shape<N>::TcY, min_blocks<T, Shape<N>::EY>(TW * Shape<N>::TcY))
+// XP: exact-add stages (FP32 only).
+template <int N, bool XP> constexpr int col_elems() { return XP ? Shape<N>::EYX : Shape<N>::EY; }
+
+template <typename T, int N, int DIR, int TW, bool XP>
+__global__ void __launch_bounds__(TW * (N / col_elems<N, XP>()), min_blocks<T, col_elems<N, XP>()>(TW * (N / col_elems<N, XP>())))
     k_fft_y(cx<T>* __restrict__ data, int64_t spec_stride, const ux<T>* __restrict__ twf, int n2_cut) {
   using C = cx<T>;
   using S = Shape<N>;
-  constexpr int NH = S::NH, E = S::EY, Tc = S::TcY;
+  constexpr int NH = S::NH, E = col_elems<N, XP>(), Tc = N / E;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int c = threadIdx.x % TW, t = threadIdx.x / TW;
@@ -285,7 +313,7 @@ __global__ void __launch_bounds__(TW * Shape<N>::TcY, min_blocks<T, Shape<N>::EY
   C v[E];
 #pragma unroll
   for (int e = 0; e < E; e++) v[e] = base[(int64_t)(t + Tc * e) * NH];
-  fft_ct<C, E, N, kInterleaved, TW, DIR>(v, sm, t, c, twf);
+  fft_any<XP, C, E, N, kInterleaved, TW, DIR>(v, sm, t, c, twf);
 #pragma unroll
   for (int e = 0; e < E; e++) {
     const int ny = sfreq<N>(t + Tc * e);
@@ -294,12 +322,13 @@ __global__ void __launch_bounds__(TW * Shape<N>::TcY, min_blocks<T, Shape<N>::EY
 }
 
 // ------------------------------------------------------------------ pass x (plain)
-template <typename T, int N, int DIR>
-__global__ void __launch_bounds__(Shape<N>::CTX, min_blocks<T, Shape<N>::EX>(Shape<N>::CTX))
+template <typename T, int N, int DIR, bool XP>
+__global__ void __launch_bounds__(Shape<N>::TW * (N / col_elems<N, XP>()),
+                                  min_blocks<T, col_elems<N, XP>()>(Shape<N>::TW * (N / col_elems<N, XP>())))
     k_fft_x(const cx<T>* in, cx<T>* out, const ux<T>* __restrict__ twf) {
   using C = cx<T>;
   using S = Shape<N>;
-  constexpr int NH = S::NH, E = S::EX, Tc = S::TcX, TW = S::TW;
+  constexpr int NH = S::NH, E = col_elems<N, XP>(), Tc = N / E, TW = S::TW;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int c = threadIdx.x % TW, t = threadIdx.x / TW;
@@ -310,7 +339,7 @@ __global__ void __launch_bounds__(Shape<N>::CTX, min_blocks<T, Shape<N>::EX>(Sha
   C v[E];
 #pragma unroll
   for (int e = 0; e < E; e++) v[e] = in[off + (t + Tc * e) * si];
-  fft_ct<C, E, N, kInterleaved, TW, DIR>(v, sm, t, c, twf);
+  fft_any<XP, C, E, N, kInterleaved, TW, DIR>(v, sm, t, c, twf);
 #pragma unroll
   for (int e = 0; e < E; e++) out[off + (t + Tc * e) * si] = v[e];
 }
@@ -396,7 +425,7 @@ __global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T, Shape<N>::E>(Shape
 // product gives Re[G conj(i F0)] = Im[G conj(F0)].
 template <typename C> __device__ __forceinline__ C f0_for(C f, int odd) { return odd ? mk(-f.y, f.x) : f; }
 
-template <typename T, int N, bool YT>
+template <typename T, int N, bool YT, bool XP>
 __global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T, Shape<N>::E>(Shape<N>::CT))
     k_bin_x(const cx<T>* G, int64_t spec_stride, int ell, int h0, int M, const cx<T>* __restrict__ F0,
             const ux<T>* __restrict__ twf, int slot, BinArgs ba, const float* __restrict__ ytab,
@@ -444,7 +473,7 @@ __global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T, Shape<N>::E>(Shape
         v[e] = Gs[off + (t + Tc * e) * si];
         if constexpr (YT) yv[e] = __ldg(Ys + (t + Tc * e) * si);
       }
-      fft_ct<C, E, N, kInterleaved, TW, -1>(v, sm, t, c, twf);
+      fft_any<XP, C, E, N, kInterleaved, TW, -1>(v, sm, t, c, twf);
 #pragma unroll
       for (int e = 0; e < E; e++) {
         const T fx = T(sfreq<N>(t + Tc * e));
@@ -513,7 +542,7 @@ template <int NPEND> __device__ __forceinline__ void cp_async_wait() {
 // other half of a double buffer, so the x pass no longer waits on global loads; the landed G
 // tile also serves as the transform's exchange buffer, and F0 stays in registers (each thread
 // owns its modes for the whole tile).
-template <int N>
+template <int N, bool XP>
 __global__ void __launch_bounds__(Shape<N>::CT, min_blocks<float, Shape<N>::E>(Shape<N>::CT))
     k_bin_x_pipe(const float2* G, int64_t spec_stride, int ell, int h0, int M, const float2* __restrict__ F0,
                  const float4* __restrict__ twf, int slot, BinArgs ba, const float* __restrict__ ytab) {
@@ -583,7 +612,7 @@ __global__ void __launch_bounds__(Shape<N>::CT, min_blocks<float, Shape<N>::E>(S
         yv[e] = ty[(t + Tc * e) * TW + c];
       }
       __syncthreads();  // the tile becomes the transform's exchange buffer
-      fft_ct<C, E, N, kInterleaved, TW, -1>(v, tg, t, c, twf);
+      fft_any<XP, C, E, N, kInterleaved, TW, -1>(v, tg, t, c, twf);
 #pragma unroll
       for (int e = 0; e < E; e++) acc[e] += yv[e] * (v[e].x * f0[e].x + v[e].y * f0[e].y);  // Y(k=0) = 0
     }
@@ -638,73 +667,98 @@ template <typename T, int N> struct Passes {
     set_smem(k_r2c_z<T, N>, smem);
     k_r2c_z<T, N><<<N * N / S::ROWS, S::ZT, smem, s>>>(in, out, twh, twr);
   }
-  static void c2r_z(const C* in, T* out, const U* twh, const U* twr, T scale, cudaStream_t s) {
-    const size_t smem = (size_t)S::ROWS * padded_len(S::NH) * sizeof(C);
-    set_smem(k_c2r_z<T, N>, smem);
-    k_c2r_z<T, N><<<N * N / S::ROWS, S::ZT, smem, s>>>(in, out, twh, twr, scale);
+  // Launchers taking `xp` run the exact-add variant of their kernel when it is set (FP32 only).
+  template <bool XP> static void c2r_z_v(const C* in, T* out, const U* twh, const U* twr, T scale, cudaStream_t s) {
+    using Z = ZShape<N, XP>;
+    const size_t smem = (size_t)Z::ROWS * padded_len(S::NH) * sizeof(C);
+    set_smem(k_c2r_z<T, N, XP>, smem);
+    k_c2r_z<T, N, XP><<<N * N / Z::ROWS, Z::ZT, smem, s>>>(in, out, twh, twr, scale);
+  }
+  static void c2r_z(const C* in, T* out, const U* twh, const U* twr, T scale, int xp, cudaStream_t s) {
+    if (sizeof(T) == 4 && xp)
+      c2r_z_v<sizeof(T) == 4>(in, out, twh, twr, scale, s);
+    else
+      c2r_z_v<false>(in, out, twh, twr, scale, s);
   }
   static size_t smem_ylm(int M, int rows) {
     const size_t stage = (size_t)M * rows * N * sizeof(T);
     const size_t xb = (size_t)M * rows * padded_len(S::NH) * sizeof(C);
     return stage > xb ? stage : xb;
   }
-  static void ylm_z(const T* f, C* out, int64_t stride, int ell, int h0, int M, const U* twh, const U* twr,
-                    const T* axis, int rows, cudaStream_t s) {
+  template <int LT, bool XP>
+  static void ylm_z_v(const T* f, C* out, int64_t stride, int ell, int h0, int M, const U* twh, const U* twr,
+                      const T* axis, int rows, cudaStream_t s) {
     const size_t smem = smem_ylm(M, rows);
-    const dim3 grid(N * N / rows), block(M * rows * S::Tz);
+    const dim3 grid(N * N / rows), block(M * rows * ZShape<N, XP>::Tz);
+    set_smem(k_ylm_r2c_z<T, N, LT, XP>, smem);
+    k_ylm_r2c_z<T, N, LT, XP><<<grid, block, smem, s>>>(f, out, stride, ell, h0, M, twh, twr, axis, rows, host_ytab<T>());
+  }
+  template <bool XP>
+  static void ylm_z_x(const T* f, C* out, int64_t stride, int ell, int h0, int M, const U* twh, const U* twr,
+                      const T* axis, int rows, cudaStream_t s) {
     switch (ell) {  // the headline multipoles get unrolled recurrences
-      case 2:
-        set_smem(k_ylm_r2c_z<T, N, 2>, smem);
-        k_ylm_r2c_z<T, N, 2><<<grid, block, smem, s>>>(f, out, stride, ell, h0, M, twh, twr, axis, rows, host_ytab<T>());
-        break;
-      case 4:
-        set_smem(k_ylm_r2c_z<T, N, 4>, smem);
-        k_ylm_r2c_z<T, N, 4><<<grid, block, smem, s>>>(f, out, stride, ell, h0, M, twh, twr, axis, rows, host_ytab<T>());
-        break;
-      case -2:  // Cartesian monomials of degree 2 (h = monomial index)
-        set_smem(k_ylm_r2c_z<T, N, -2>, smem);
-        k_ylm_r2c_z<T, N, -2><<<grid, block, smem, s>>>(f, out, stride, ell, h0, M, twh, twr, axis, rows, host_ytab<T>());
-        break;
-      case -4:
-        set_smem(k_ylm_r2c_z<T, N, -4>, smem);
-        k_ylm_r2c_z<T, N, -4><<<grid, block, smem, s>>>(f, out, stride, ell, h0, M, twh, twr, axis, rows, host_ytab<T>());
-        break;
-      default:
-        set_smem(k_ylm_r2c_z<T, N, 0>, smem);
-        k_ylm_r2c_z<T, N, 0><<<grid, block, smem, s>>>(f, out, stride, ell, h0, M, twh, twr, axis, rows, host_ytab<T>());
+      case 2: ylm_z_v<2, XP>(f, out, stride, ell, h0, M, twh, twr, axis, rows, s); break;
+      case 4: ylm_z_v<4, XP>(f, out, stride, ell, h0, M, twh, twr, axis, rows, s); break;
+      // Cartesian monomials of degree 2 and 4 (h = monomial index)
+      case -2: ylm_z_v<-2, XP>(f, out, stride, ell, h0, M, twh, twr, axis, rows, s); break;
+      case -4: ylm_z_v<-4, XP>(f, out, stride, ell, h0, M, twh, twr, axis, rows, s); break;
+      default: ylm_z_v<0, XP>(f, out, stride, ell, h0, M, twh, twr, axis, rows, s);
     }
+  }
+  static void ylm_z(const T* f, C* out, int64_t stride, int ell, int h0, int M, const U* twh, const U* twr,
+                    const T* axis, int rows, int xp, cudaStream_t s) {
+    if (sizeof(T) == 4 && xp)
+      ylm_z_x<sizeof(T) == 4>(f, out, stride, ell, h0, M, twh, twr, axis, rows, s);
+    else
+      ylm_z_x<false>(f, out, stride, ell, h0, M, twh, twr, axis, rows, s);
   }
   // variant 0: TW columns per block; variant 1: TW/2 (half the threads and shared memory)
-  template <int TWV>
+  template <int TWV, bool XP>
   static void fft_y_tw(C* data, int64_t stride, int nspec, const U* twf, int dir, int n2_cut, cudaStream_t s) {
     const size_t smem = (size_t)N * TWV * sizeof(C);
+    const int threads = TWV * (N / col_elems<N, XP>());
     dim3 grid(N * (S::NH / TWV), nspec);
     if (dir < 0) {
-      set_smem(k_fft_y<T, N, -1, TWV>, smem);
-      k_fft_y<T, N, -1, TWV><<<grid, TWV * S::TcY, smem, s>>>(data, stride, twf, n2_cut);
+      set_smem(k_fft_y<T, N, -1, TWV, XP>, smem);
+      k_fft_y<T, N, -1, TWV, XP><<<grid, threads, smem, s>>>(data, stride, twf, n2_cut);
     } else {
-      set_smem(k_fft_y<T, N, 1, TWV>, smem);
-      k_fft_y<T, N, 1, TWV><<<grid, TWV * S::TcY, smem, s>>>(data, stride, twf, n2_cut);
+      set_smem(k_fft_y<T, N, 1, TWV, XP>, smem);
+      k_fft_y<T, N, 1, TWV, XP><<<grid, threads, smem, s>>>(data, stride, twf, n2_cut);
     }
   }
-  static void fft_y(C* data, int64_t stride, int nspec, const U* twf, int dir, int variant, int n2_cut,
-                    cudaStream_t s) {
+  template <bool XP>
+  static void fft_y_x(C* data, int64_t stride, int nspec, const U* twf, int dir, int variant, int n2_cut,
+                      cudaStream_t s) {
     constexpr int TW2 = S::TW > 1 ? S::TW / 2 : 1;
     if (variant == 1 && S::TW > 1)
-      fft_y_tw<TW2>(data, stride, nspec, twf, dir, n2_cut, s);
+      fft_y_tw<TW2, XP>(data, stride, nspec, twf, dir, n2_cut, s);
     else
-      fft_y_tw<S::TW>(data, stride, nspec, twf, dir, n2_cut, s);
+      fft_y_tw<S::TW, XP>(data, stride, nspec, twf, dir, n2_cut, s);
   }
-  static void fft_x(const C* in, C* out, const U* twf, int dir, cudaStream_t s) {
+  static void fft_y(C* data, int64_t stride, int nspec, const U* twf, int dir, int variant, int n2_cut, int xp,
+                    cudaStream_t s) {
+    if (sizeof(T) == 4 && xp)
+      fft_y_x<sizeof(T) == 4>(data, stride, nspec, twf, dir, variant, n2_cut, s);
+    else
+      fft_y_x<false>(data, stride, nspec, twf, dir, variant, n2_cut, s);
+  }
+  template <bool XP> static void fft_x_v(const C* in, C* out, const U* twf, int dir, cudaStream_t s) {
     const size_t smem = smem_col();
     const unsigned grid = N * (S::NH / S::TW);
+    const int threads = S::TW * (N / col_elems<N, XP>());
     if (dir < 0) {
-      set_smem(k_fft_x<T, N, -1>, smem);
-      k_fft_x<T, N, -1><<<grid, S::CTX, smem, s>>>(in, out, twf);
+      set_smem(k_fft_x<T, N, -1, XP>, smem);
+      k_fft_x<T, N, -1, XP><<<grid, threads, smem, s>>>(in, out, twf);
     } else {
-      set_smem(k_fft_x<T, N, 1>, smem);
-      k_fft_x<T, N, 1><<<grid, S::CTX, smem, s>>>(in, out, twf);
+      set_smem(k_fft_x<T, N, 1, XP>, smem);
+      k_fft_x<T, N, 1, XP><<<grid, threads, smem, s>>>(in, out, twf);
     }
+  }
+  static void fft_x(const C* in, C* out, const U* twf, int dir, int xp, cudaStream_t s) {
+    if (sizeof(T) == 4 && xp)
+      fft_x_v<sizeof(T) == 4>(in, out, twf, dir, s);
+    else
+      fft_x_v<false>(in, out, twf, dir, s);
   }
   static void combine_x(const C* B, C* F0, const U* twf, int interlaced, int compensate, int roundtrip,
                         const U* phase, const C* invw, const BinArgs& ba, int ctas, cudaStream_t s) {
@@ -712,26 +766,34 @@ template <typename T, int N> struct Passes {
     set_smem(k_combine_x<T, N>, smem);
     k_combine_x<T, N><<<ctas, S::CT, smem, s>>>(B, F0, twf, interlaced, compensate, roundtrip, phase, invw, ba);
   }
-  static void bin_x(const C* G, int64_t stride, int ell, int h0, int M, const C* F0, const U* twf, int slot,
-                    const BinArgs& ba, int ctas, const float* ytab, cudaStream_t s) {
+  template <bool XP>
+  static void bin_x_v(const C* G, int64_t stride, int ell, int h0, int M, const C* F0, const U* twf, int slot,
+                      const BinArgs& ba, int ctas, const float* ytab, cudaStream_t s) {
     const size_t smem = smem_bin(ba.nk);
     if constexpr (sizeof(T) == 4 && S::E == 8) {
       if (ytab) {
         const size_t sp = smem_bin_pipe(ba.nk);
-        set_smem(k_bin_x_pipe<N>, sp);
-        k_bin_x_pipe<N><<<ctas, S::CT, sp, s>>>(G, stride, ell, h0, M, F0, twf, slot, ba, ytab);
+        set_smem(k_bin_x_pipe<N, XP>, sp);
+        k_bin_x_pipe<N, XP><<<ctas, S::CT, sp, s>>>(G, stride, ell, h0, M, F0, twf, slot, ba, ytab);
         return;
       }
     }
     if (ytab && sizeof(T) == 4) {
-      set_smem(k_bin_x<T, N, true>, smem);
-      k_bin_x<T, N, true><<<ctas, S::CT, smem, s>>>(G, stride, ell, h0, M, F0, twf, slot, ba, ytab, host_ytab<T>());
+      set_smem(k_bin_x<T, N, true, XP>, smem);
+      k_bin_x<T, N, true, XP><<<ctas, S::CT, smem, s>>>(G, stride, ell, h0, M, F0, twf, slot, ba, ytab, host_ytab<T>());
     } else {
-      set_smem(k_bin_x<T, N, false>, smem);
-      k_bin_x<T, N, false><<<ctas, S::CT, smem, s>>>(G, stride, ell, h0, M, F0, twf, slot, ba, ytab, host_ytab<T>());
+      set_smem(k_bin_x<T, N, false, XP>, smem);
+      k_bin_x<T, N, false, XP><<<ctas, S::CT, smem, s>>>(G, stride, ell, h0, M, F0, twf, slot, ba, ytab, host_ytab<T>());
     }
   }
-  static int ctas(int which, int nk, int nsm) {
+  static void bin_x(const C* G, int64_t stride, int ell, int h0, int M, const C* F0, const U* twf, int slot,
+                    const BinArgs& ba, int ctas, const float* ytab, int xp, cudaStream_t s) {
+    if (sizeof(T) == 4 && xp)
+      bin_x_v<sizeof(T) == 4>(G, stride, ell, h0, M, F0, twf, slot, ba, ctas, ytab, s);
+    else
+      bin_x_v<false>(G, stride, ell, h0, M, F0, twf, slot, ba, ctas, ytab, s);
+  }
+  template <bool XP> static int ctas_v(int which, int nk, int nsm) {
     int per = 0;
     if (which == 0) {
       const size_t smem = smem_combine(nk);
@@ -740,21 +802,25 @@ template <typename T, int N> struct Passes {
     } else if (which == 2 && sizeof(T) == 4 && S::E == 8) {
       if constexpr (sizeof(T) == 4 && S::E == 8) {
         const size_t smem = smem_bin_pipe(nk);
-        set_smem(k_bin_x_pipe<N>, smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bin_x_pipe<N>, S::CT, smem);
+        set_smem(k_bin_x_pipe<N, XP>, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bin_x_pipe<N, XP>, S::CT, smem);
       }
     } else if (which == 2) {
       const size_t smem = smem_bin(nk);
-      set_smem(k_bin_x<T, N, true>, smem);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bin_x<T, N, true>, S::CT, smem);
+      set_smem(k_bin_x<T, N, true, XP>, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bin_x<T, N, true, XP>, S::CT, smem);
     } else {
       const size_t smem = smem_bin(nk);
-      set_smem(k_bin_x<T, N, false>, smem);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bin_x<T, N, false>, S::CT, smem);
+      set_smem(k_bin_x<T, N, false, XP>, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bin_x<T, N, false, XP>, S::CT, smem);
     }
     if (per < 1) per = 1;
     const int ntiles = N * (S::NH / S::TW);
     return per * nsm < ntiles ? per * nsm : ntiles;
+  }
+  static int ctas(int which, int nk, int nsm, int xp) {
+    if (sizeof(T) == 4 && xp) return ctas_v<sizeof(T) == 4>(which, nk, nsm);
+    return ctas_v<false>(which, nk, nsm);
   }
   static PassTable<T> table() {
     PassTable<T> t;
@@ -763,6 +829,7 @@ template <typename T, int N> struct Passes {
     t.tw = S::TW;
     t.rows_z = S::ROWS;
     t.tz = S::Tz;
+    t.tz_xp = ZShape<N, sizeof(T) == 4>::Tz;
     t.r2c_z = &r2c_z;
     t.c2r_z = &c2r_z;
     t.ylm_z = &ylm_z;

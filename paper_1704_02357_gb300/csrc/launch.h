@@ -130,7 +130,9 @@ constexpr int z_rows(int N) {
 // 160 (5 x 16 x 2); capping them there keeps them within 56 registers, so that 4 and 7 blocks
 // share an SM instead of 3 and 6.
 __host__ __device__ constexpr int ylm_thread_cap(int lt) { return lt == 4 ? 288 : (lt == 2 ? 160 : 512); }
-__host__ __device__ constexpr int ylm_min_blocks(int lt) { return lt == 4 ? 4 : (lt == 2 ? 7 : 0); }
+__host__ __device__ constexpr int ylm_min_blocks(int lt, bool xp = false) {
+  return xp ? (lt == 4 ? 2 : (lt == 2 ? 4 : 0)) : (lt == 4 ? 4 : (lt == 2 ? 7 : 0));
+}
 
 // Twiddle and phase tables hold ux<T> entries (FP32: {cos, sin, 1/|w| - 1, 0}); the
 // compensation table holds cx<T> {1/W_d rounded, its relative rounding error}.
@@ -145,20 +147,24 @@ void launch_ytab_build(float* ytab, int N, int ell_max, int nsm, cudaStream_t s)
 // Cartesian k-space factors mult_q khat^q of every stored mode, q = 0..20 (kCartItems slots).
 void launch_ctab_build(float* ctab, int N, int nsm, cudaStream_t s);
 
+// Launchers with an `xp` argument run the exact-add FP32 variant of their kernel (xp_engine.cuh)
+// when it is nonzero and T is float; FP64 ignores it.
 template <typename T> struct PassTable {
   int N, E, tw, rows_z, tz;
+  int tz_xp;  // threads per row of the exact-add z passes
   void (*r2c_z)(const T*, cx<T>*, const ux<T>*, const ux<T>*, cudaStream_t);
-  void (*c2r_z)(const cx<T>*, T*, const ux<T>*, const ux<T>*, T, cudaStream_t);
-  void (*ylm_z)(const T*, cx<T>*, int64_t, int, int, int, const ux<T>*, const ux<T>*, const T*, int, cudaStream_t);
+  void (*c2r_z)(const cx<T>*, T*, const ux<T>*, const ux<T>*, T, int, cudaStream_t);
+  void (*ylm_z)(const T*, cx<T>*, int64_t, int, int, int, const ux<T>*, const ux<T>*, const T*, int, int,
+                cudaStream_t);
   size_t (*smem_ylm)(int, int);
-  // ..., dir, tile variant, n2_cut (outputs with ny^2 + kz^2 >= n2_cut are not stored)
-  void (*fft_y)(cx<T>*, int64_t, int, const ux<T>*, int, int, int, cudaStream_t);
-  void (*fft_x)(const cx<T>*, cx<T>*, const ux<T>*, int, cudaStream_t);
+  // ..., dir, tile variant, n2_cut (outputs with ny^2 + kz^2 >= n2_cut are not stored), xp
+  void (*fft_y)(cx<T>*, int64_t, int, const ux<T>*, int, int, int, int, cudaStream_t);
+  void (*fft_x)(const cx<T>*, cx<T>*, const ux<T>*, int, int, cudaStream_t);
   void (*combine_x)(const cx<T>*, cx<T>*, const ux<T>*, int, int, int, const ux<T>*, const cx<T>*, const BinArgs&,
                     int, cudaStream_t);
   void (*bin_x)(const cx<T>*, int64_t, int, int, int, const cx<T>*, const ux<T>*, int, const BinArgs&, int,
-                const float*, cudaStream_t);  // ..., table slot of the group's first harmonic, or nullptr
-  int (*ctas)(int, int, int);  // (which: 0 combine, 1 bin, 2 pipelined FP32 bin; nk; SMs) -> persistent blocks
+                const float*, int, cudaStream_t);  // ..., table slot of the group's first harmonic or nullptr, xp
+  int (*ctas)(int, int, int, int);  // (which: 0 combine, 1 bin, 2 pipelined FP32 bin; nk; SMs; xp) -> persistent blocks
   size_t (*smem_combine)(int);
   size_t (*smem_bin)(int);
   size_t (*smem_bin_pipe)(int);

@@ -49,6 +49,7 @@ struct Plan {
   int ctas_comb, ctas_bin, ctas_bin_plain;  // plain: the binning kernel without the Y table
   int nblk_sum;
   bool roundtrip;
+  int xp;  // FP32 harmonic and inverse transforms in exact-add stages
   size_t Sr, Sc;
   int n2max;
   // workspace offsets
@@ -69,7 +70,7 @@ pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl,
   if (!good_nmesh(p->nmesh)) { *why = "nmesh must be even, 16..1024 and 2^a, or 48..768 and 3*2^a"; return PSPEC_EUNSUPPORTED; }
   if (p->window != PSPEC_WINDOW_CIC && p->window != PSPEC_WINDOW_TSC) { *why = "window must be CIC or TSC"; return PSPEC_EINVAL; }
   if (p->compensate < 0 || p->compensate > 3) { *why = "compensate must be 0..3"; return PSPEC_EINVAL; }
-  if (p->precision != PSPEC_FP32 && p->precision != PSPEC_FP64) { *why = "precision must be FP32 or FP64"; return PSPEC_EINVAL; }
+  if (p->precision != PSPEC_FP32 && p->precision != PSPEC_FP64 && p->precision != PSPEC_FP32_PLAIN) { *why = "precision must be FP32, FP32_PLAIN or FP64"; return PSPEC_EINVAL; }
   if (p->ell_max < 0) { *why = "ell_max must be >= 0"; return PSPEC_EUNSUPPORTED; }
   if (p->ell_max > PSPEC_MAX_ELL) { *why = "ell_max > 16"; return PSPEC_EUNSUPPORTED; }
   if (!(std::isfinite(p->box_size) && p->box_size > 0)) { *why = "box_size must be finite and > 0"; return PSPEC_EINVAL; }
@@ -84,6 +85,9 @@ pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl,
   if (p->max_particles < 0 || p->max_particles > (int64_t)0xfffffff0) { *why = "max_particles out of range"; return PSPEC_EINVAL; }
 
   const bool f64 = p->precision == PSPEC_FP64;
+  // FP32: the harmonic transforms and the inverse transform of the round trip in exact-add
+  // stages (xp_engine.cuh); FP32_PLAIN: every transform a plain FP32 radix tree
+  pl->xp = p->precision == PSPEC_FP32 ? 1 : 0;
   const int N = p->nmesh, NH = N / 2;
   pl->g.N = N;
   pl->g.NH = NH;
@@ -120,12 +124,12 @@ pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl,
     if (need > kSmemMaxBlock) { *why = "max_kbins too large for this mesh (shared memory)"; return PSPEC_EINVAL; }
   }
   if (f64) {
-    pl->ctas_comb = pl->td->ctas(0, max_kbins, nsm);
-    pl->ctas_bin = pl->ctas_bin_plain = pl->td->ctas(1, max_kbins, nsm);
+    pl->ctas_comb = pl->td->ctas(0, max_kbins, nsm, 0);
+    pl->ctas_bin = pl->ctas_bin_plain = pl->td->ctas(1, max_kbins, nsm, 0);
   } else {
-    pl->ctas_comb = pl->tf->ctas(0, max_kbins, nsm);
-    pl->ctas_bin = pl->tf->ctas(pl->has_ytab ? 2 : 1, max_kbins, nsm);
-    pl->ctas_bin_plain = pl->tf->ctas(1, max_kbins, nsm);
+    pl->ctas_comb = pl->tf->ctas(0, max_kbins, nsm, pl->xp);
+    pl->ctas_bin = pl->tf->ctas(pl->has_ytab ? 2 : 1, max_kbins, nsm, pl->xp);
+    pl->ctas_bin_plain = pl->tf->ctas(1, max_kbins, nsm, pl->xp);
   }
   pl->nblk_sum = 2 * nsm;
 
@@ -580,12 +584,12 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
 
   // a3: F1 (and F2), combine + compensate -> F0 with the l = 0 sums; round trip -> f
   TRY(run(c, PSPEC_K_FFT_Z, acc(Sr + Sc), [&] { PT->r2c_z(m1, F0, twh, twr, s); }));
-  TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { PT->fft_y(F0, 0, 1, twf, -1, c->tune.tile_y, INT_MAX, s); }));
+  TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { PT->fft_y(F0, 0, 1, twf, -1, c->tune.tile_y, INT_MAX, 0, s); }));
   transforms++;
   if (c->p.interlaced) {
-    TRY(run(c, PSPEC_K_FFT_X, acc(2 * Sc), [&] { PT->fft_x(F0, F0, twf, -1, s); }));
+    TRY(run(c, PSPEC_K_FFT_X, acc(2 * Sc), [&] { PT->fft_x(F0, F0, twf, -1, 0, s); }));
     TRY(run(c, PSPEC_K_FFT_Z, acc(Sr + Sc), [&] { PT->r2c_z(m2, W, twh, twr, s); }));
-    TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { PT->fft_y(W, 0, 1, twf, -1, c->tune.tile_y, INT_MAX, s); }));
+    TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { PT->fft_y(W, 0, 1, twf, -1, c->tune.tile_y, INT_MAX, 0, s); }));
     transforms++;
     TRY(run(c, PSPEC_K_COMBINE, acc(3 * Sc), [&] {
       PT->combine_x(W, F0, twf, 1, c->p.compensate, pl.roundtrip, phase, invw, ba, ctas_comb, s);
@@ -596,10 +600,10 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
     }));
   }
   if (pl.roundtrip) {
-    TRY(run(c, PSPEC_K_FFT_X, acc(2 * Sc), [&] { PT->fft_x(F0, W, twf, +1, s); }));
-    TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { PT->fft_y(W, 0, 1, twf, +1, c->tune.tile_y, INT_MAX, s); }));
+    TRY(run(c, PSPEC_K_FFT_X, acc(2 * Sc), [&] { PT->fft_x(F0, W, twf, +1, pl.xp, s); }));
+    TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { PT->fft_y(W, 0, 1, twf, +1, c->tune.tile_y, INT_MAX, pl.xp, s); }));
     const T scale = T(2.0 / ((double)N * N * N));
-    TRY(run(c, PSPEC_K_C2R_Z, acc(Sc + Sr), [&] { PT->c2r_z(W, f, twh, twr, scale, s); }));
+    TRY(run(c, PSPEC_K_C2R_Z, acc(Sc + Sr), [&] { PT->c2r_z(W, f, twh, twr, scale, pl.xp, s); }));
     transforms++;
   }
 
@@ -641,7 +645,7 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
     for (int h0 = hlo; h0 < hhi; h0 += pl.group_max) {
       const int M = std::min(pl.group_max, hhi - h0);
       // z pass with the Y_lm weights: one block holds Ms harmonics x rows rows, tz threads each
-      const int tz = PT->tz;
+      const int tz = pl.xp ? PT->tz_xp : PT->tz;
       const int cap = ylm_thread_cap(ell);
       const int ms_max = std::max(1, std::min(c->tune.ylm_harmonics, cap / tz));
       for (int hs = 0; hs < M; hs += ms_max) {
@@ -649,17 +653,17 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
         int rows = std::max(1, pow2_floor(std::max(1, cap / (Ms * tz))));
         while (rows > 1 && (((int64_t)N * N) % rows || PT->smem_ylm(Ms, rows) > kSmemBudget)) rows >>= 1;
         TRY(run(c, PSPEC_K_YLM_Z, acc(Sr + Ms * Sc), [&] {
-          PT->ylm_z(f, G + hs * stride, stride, ell, h0 + hs, Ms, twh, twr, axis, rows, s);
+          PT->ylm_z(f, G + hs * stride, stride, ell, h0 + hs, Ms, twh, twr, axis, rows, pl.xp, s);
         }));
       }
       TRY(run(c, PSPEC_K_FFT_Y, acc(M * Sc * (c->frac_yr + c->frac_yw)),
-              [&] { PT->fft_y(G, stride, M, twf, -1, c->tune.tile_y, c->n2_cut, s); }));
+              [&] { PT->fft_y(G, stride, M, twf, -1, c->tune.tile_y, c->n2_cut, pl.xp, s); }));
       const float* ytab = jobs[jb].table ? jobs[jb].table + (int64_t)h0 * stride : nullptr;
       const double ybytes = ytab ? M * (double)N * N * g.NH * sizeof(float) : 0.0;
       BinArgs bj = ba;
       bj.odd = ell > 0 && (ell & 1);
       TRY(run(c, PSPEC_K_BIN_X, acc((Sc + M * Sc + ybytes) * c->frac_tile), [&] {
-        PT->bin_x(G, stride, ell, h0, M, F0, twf, jobs[jb].slot, bj, ytab ? ctas_bin : ctas_bin_plain, ytab, s);
+        PT->bin_x(G, stride, ell, h0, M, F0, twf, jobs[jb].slot, bj, ytab ? ctas_bin : ctas_bin_plain, ytab, pl.xp, s);
       }));
       transforms += M;
     }
@@ -1043,7 +1047,7 @@ pspec_status pspec_run_batch(void* ctx, const pspec_catalog* mocks, int32_t n_mo
                       c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->at<int>(pl.o_cur), 0, sizeof(int), c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "batch table upload");
-  const bool binned = c->tune.paint_binned && pl.max_particles >= max_count && c->p.precision == PSPEC_FP32;
+  const bool binned = c->tune.paint_binned && pl.max_particles >= max_count && c->p.precision != PSPEC_FP64;
   const bool f64 = c->p.precision == PSPEC_FP64;
   auto one = [&]() {
     return f64 ? enqueue_mock<double>(c, binned, max_count, ells, n_ells, n_kbins, P_all, sums_all)
@@ -1210,7 +1214,7 @@ pspec_status pspec_autotune(void* ctx, const pspec_catalog* data, const pspec_ca
   float best_ms = 0.f;
   pspec_status st = measure(cur, &best_ms);
   // coordinate search over the knobs
-  const int tz = pass_table<float>(c->p.nmesh)->tz;
+  const int tz = c->pl.xp ? pass_table<float>(c->p.nmesh)->tz_xp : pass_table<float>(c->p.nmesh)->tz;
   const int hmax = std::max(1, 512 / tz);
   std::vector<std::vector<int>> cand = {
       {1, 0}, {hmax, std::max(1, hmax / 2), std::max(1, hmax / 4)}, {0, 1, 2}, {0, 1}};

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_PKG, "libpspec.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ECANCELED, EUNSUPPORTED, ESTATE = range(8)
 WINDOWS = {"cic": 2, "tsc": 3}
-PRECISIONS = {"fp32": 0, "fp64": 1}
+PRECISIONS = {"fp32": 0, "fp64": 1, "fp32_plain": 2}
 K_NAMES = ["catalog_sums", "paint", "r2c_z", "fft_y", "fft_x", "combine_x", "ylm_r2c_z", "bin_x",
            "c2r_z", "finalize", "other"]
 

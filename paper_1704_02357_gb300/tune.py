@@ -17,7 +17,7 @@ def key_for(est) -> str:
     import torch
     p = est.params
     name = torch.cuda.get_device_name(est.device).replace(" ", "_")
-    prec = "fp64" if p.precision else "fp32"
+    prec = {0: "fp32", 1: "fp64", 2: "fp32_plain"}.get(p.precision, str(p.precision))
     return f"{name}|N{p.nmesh}|{prec}|l{p.ell_max}|w{p.window}|i{p.interlaced}"
 
 
