@@ -91,8 +91,12 @@ typedef struct {
   double P0;               /* FKP P0; 0 gives w_fkp = 1 */
   double nbar;             /* n̄ used for particles whose catalog has no nbar array */
   int64_t max_group_bytes; /* cap on the per-group spectrum buffers; 0 = one whole multipole */
-  int64_t max_particles;   /* data + randoms the tile-binned paint is sized for (FP32 meshes);
-                              0, a larger catalog pair or FP64 meshes use direct atomic painting */
+  int64_t max_particles;   /* data + randoms the tile-binned paint is sized for (FP32 meshes;
+                              148 bytes of workspace per particle). That paint sums each cell
+                              exactly (64-bit fixed point) and rounds it once, so the meshes do
+                              not depend on the order of the additions. 0, a larger catalog pair
+                              or FP64 meshes use direct atomic painting (FP32 meshes: atomics in
+                              FP32, whose rounding depends on the order of the additions) */
   int32_t cache_randoms;   /* 0/1: reserve meshes for pspec_set_randoms / pspec_run_batch */
   int32_t ylm_table;       /* FP32 contexts, l_max >= 2: 0 = hold Y_lm(khat) of every stored mode
                               for l = 2..l_max, evaluated in FP64 at creation and rounded once
@@ -106,6 +110,13 @@ typedef struct {
                               512^3) for pspec_multipoles_cartesian */
 } pspec_params;
 #define PSPEC_YLM_TABLE_AUTO_MAX ((int64_t)64 << 30)
+/* With ylm_table = 0, FP32 contexts also hold Y_lm(rhat) of every mesh node for l = 2..l_max
+ * (even l), evaluated in FP64 at creation and rounded once to FP32 (4 bytes per node and
+ * harmonic: 7.5 GB at 512^3, l_max = 4; 82 GB at l_max = 16), when that takes at most
+ * PSPEC_YLM_RTABLE_AUTO_MAX bytes. The Y-weighted transforms read their weights from it;
+ * without it they evaluate Y_lm(rhat) in FP32, whose errors are coherent over the sphere and
+ * leak ~1e-4 of P_14 (and ~2e-5 of a small P_4) at 512^3 through the shot noise. */
+#define PSPEC_YLM_RTABLE_AUTO_MAX ((int64_t)96 << 30)
 
 typedef struct {
   const void* pos;         /* device, count x 3 row-major, dtype per pos_dtype */
@@ -295,6 +306,7 @@ typedef struct {
   double model_bytes_last;                    /* algorithmic HBM bytes of the last paint+multipoles */
   int64_t ylm_table_bytes;                    /* Y_lm(khat) table held (0: evaluated per mode) */
   int64_t cartesian_table_bytes;              /* Cartesian k-space factors held (0: none) */
+  int64_t ylm_rtable_bytes;                   /* Y_lm(rhat) table held (0: evaluated per node) */
 } pspec_plan_info;
 pspec_status pspec_get_plan_info(void* ctx, pspec_plan_info* info);
 

@@ -221,32 +221,35 @@ template <typename C> struct Dft<C, 3> {
 // Y_{l,-a} = sqrt2 q_l^a Im(x+iy)^a. Tables are computed in FP64 on the host.
 constexpr int kLmax = 16;
 constexpr int kLdim = kLmax + 1;
-// In FP32 the coefficients A and B are split into hi + lo (lo = the rounding error of hi)
-// and lo enters the roundings of the exact products: rounded coefficients alone would change
-// the shape of q_l^a(z) by ~1e-7, an error smooth over the sphere whose shell averages are
-// not zero, through which the k-independent shot-noise term leaks into P_l (l >= 2).
+// The recurrence runs on q_l^a / c_a (seed 1) and the constant factor n_a (c_0 for a = 0,
+// sqrt2 c_a for a > 0) is applied last. In FP32 the coefficients A, B and n_a are split into
+// hi + lo (lo = the rounding error of hi) and lo enters the roundings of the exact products:
+// rounded coefficients alone would change the shape of q_l^a(z) by ~1e-7, an error smooth over
+// the sphere whose shell averages are not zero, and a rounded n_a would scale a whole harmonic
+// by up to 3e-8; through either, the k-independent shot-noise term leaks into P_l (l >= 2).
 template <typename T> struct YTab {
-  T c[kLdim];
+  T n[kLdim];          // n_a
+  T nl[kLdim];         // lo part of n_a (FP32 only; zero in FP64)
   T A[kLdim * kLdim];  // [l * kLdim + a]
   T B[kLdim * kLdim];
   T Al[kLdim * kLdim];  // lo parts (FP32 only; zero in FP64)
   T Bl[kLdim * kLdim];
 };
 
-// HILO = false: coefficients rounded to T only. Both spaces use HILO = true: a coherent error
-// in the real-space weights Y_lm(rhat) leaks part of the shot noise into P_l through shell sums
-// of Y_lm(khat) that the mesh's cubic symmetry leaves nonzero, and it grows with l.
+// q_l^a(z) / c_a. HILO = false: coefficients rounded to T only. Both spaces use HILO = true:
+// a coherent error in the real-space weights Y_lm(rhat) leaks part of the shot noise into P_l
+// through shell sums of Y_lm(khat) that the mesh's cubic symmetry leaves nonzero, and it grows
+// with l.
 template <typename T, bool HILO = true>
-__device__ __forceinline__ T ylm_q(const YTab<T>& t, int ell, int a, T z) {
-  T q2 = t.c[a];
+__device__ __forceinline__ T ylm_qt(const YTab<T>& t, int ell, int a, T z) {
+  T q2 = T(1);
   if (ell == a) return q2;
   const int i1 = (a + 1) * kLdim + a;
   T q1;
   if constexpr (sizeof(T) == 4 && HILO) {
-    const T zq = z * q2;
-    q1 = fmaf(t.A[i1], zq, t.Al[i1] * zq);
+    q1 = fmaf(t.A[i1], z, t.Al[i1] * z);
   } else {
-    q1 = t.A[i1] * z * q2;
+    q1 = t.A[i1] * z;
   }
   for (int l = a + 2; l <= ell; l++) {
     const int i = l * kLdim + a;
@@ -262,6 +265,14 @@ __device__ __forceinline__ T ylm_q(const YTab<T>& t, int ell, int a, T z) {
     q1 = q;
   }
   return q1;
+}
+
+// x n_a: Y_l0 = n_0 qt; Y_{l,+a} = n_a qt Re(x+iy)^a, Y_{l,-a} = n_a qt Im(x+iy)^a.
+template <typename T> __device__ __forceinline__ T ylm_norm(const YTab<T>& t, int a, T x) {
+  if constexpr (sizeof(T) == 4)
+    return fmaf(x, t.n[a], x * t.nl[a]);
+  else
+    return x * t.n[a];
 }
 
 // Cartesian decomposition (the route the paper compares against, Sec. 2.1): monomials

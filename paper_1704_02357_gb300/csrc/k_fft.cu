@@ -60,7 +60,11 @@ template <typename T> static YTab<T> build_ytab() {
     t.Al[i] = T(0);
     t.Bl[i] = T(0);
   }
-  for (int a = 0; a < kLdim; a++) t.c[a] = T(c[a]);
+  for (int a = 0; a < kLdim; a++) {
+    const double n = a == 0 ? c[0] : std::sqrt(2.0) * c[a];
+    t.n[a] = T(n);
+    t.nl[a] = sizeof(T) == 4 ? T(n - (double)T(n)) : T(0);
+  }
   for (int l = 1; l < kLdim; l++) {
     for (int a = 0; a < l; a++) {
       const double A = std::sqrt((4.0 * l * l - 1.0) / ((double)l * l - (double)a * a));
@@ -95,7 +99,6 @@ __global__ void __launch_bounds__(256) k_ytab_build(float* __restrict__ ytab, in
                                                     const __grid_constant__ YTab<double> yt) {
   const int NH = N / 2;
   const int64_t modes = (int64_t)N * N * NH;
-  const double sq2 = 1.41421356237309504880;
   for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < modes; m += (int64_t)gridDim.x * blockDim.x) {
     const int kz = (int)(m % NH);
     const int64_t ij = m / NH;
@@ -110,7 +113,7 @@ __global__ void __launch_bounds__(256) k_ytab_build(float* __restrict__ ytab, in
       for (int l = a; l <= ell_max; l++) {
         double q;
         if (l == a)
-          q = yt.c[a];
+          q = 1.0;
         else if (l == a + 1)
           q = yt.A[l * kLdim + a] * z * qm1;
         else
@@ -123,10 +126,10 @@ __global__ void __launch_bounds__(256) k_ytab_build(float* __restrict__ ytab, in
           if (a == 0) base[0] = 0.f;
           else base[(int64_t)(2 * a - 1) * modes] = base[(int64_t)(2 * a) * modes] = 0.f;
         } else if (a == 0) {
-          base[0] = (float)q;
+          base[0] = (float)(yt.n[0] * q);
         } else {
-          base[(int64_t)(2 * a - 1) * modes] = (float)(sq2 * q * pr);
-          base[(int64_t)(2 * a) * modes] = (float)(sq2 * q * pi);
+          base[(int64_t)(2 * a - 1) * modes] = (float)(yt.n[a] * q * pr);
+          base[(int64_t)(2 * a) * modes] = (float)(yt.n[a] * q * pi);
         }
       }
       const double nr = pr * x - pi * y;
@@ -134,6 +137,59 @@ __global__ void __launch_bounds__(256) k_ytab_build(float* __restrict__ ytab, in
       pr = nr;
     }
   }
+}
+
+// ------------------------------------------------------------------ Y_lm(rhat) table
+// One thread per mesh node (i, j, k): rhat = (corner + (i, j, k) H - observer)/|.| in FP64,
+// the recurrence in l (FP64 coefficients) and (x + i y)^a, each Y_{l,m} of an even l >= 2
+// stored rounded once to FP32 at rtab[(ytab_base(l) + h) * N^3 + (i N + j) N + k]. The node at
+// the observer gets 0.
+__global__ void __launch_bounds__(256) k_rtab_build(float* __restrict__ rtab, int N, int ell_max, RGeo g,
+                                                    const __grid_constant__ YTab<double> yt) {
+  const int64_t pts = (int64_t)N * N * N;
+  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < pts; m += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(m % N);
+    const int64_t ij = m / N;
+    const int j = (int)(ij % N), i = (int)(ij / N);
+    const double vx = g.corner[0] + i * g.H - g.observer[0], vy = g.corner[1] + j * g.H - g.observer[1],
+                 vz = g.corner[2] + k * g.H - g.observer[2];
+    const double r2 = vx * vx + vy * vy + vz * vz;
+    const double inv = r2 > 0.0 ? 1.0 / sqrt(r2) : 0.0;
+    const double x = vx * inv, y = vy * inv, z = vz * inv;
+    double pr = 1.0, pi = 0.0;  // (x + i y)^a
+    for (int a = 0; a <= ell_max; a++) {
+      double qm1 = 0.0, qm2 = 0.0;
+      for (int l = a; l <= ell_max; l++) {
+        double q;
+        if (l == a)
+          q = 1.0;
+        else if (l == a + 1)
+          q = yt.A[l * kLdim + a] * z * qm1;
+        else
+          q = yt.A[l * kLdim + a] * (z * qm1 - yt.B[l * kLdim + a] * qm2);
+        qm2 = qm1;
+        qm1 = q;
+        if (l < 2 || (l & 1)) continue;
+        float* base = rtab + (int64_t)ytab_base(l) * pts + m;
+        if (r2 == 0.0) {
+          if (a == 0) base[0] = 0.f;
+          else base[(int64_t)(2 * a - 1) * pts] = base[(int64_t)(2 * a) * pts] = 0.f;
+        } else if (a == 0) {
+          base[0] = (float)(yt.n[0] * q);
+        } else {
+          base[(int64_t)(2 * a - 1) * pts] = (float)(yt.n[a] * q * pr);
+          base[(int64_t)(2 * a) * pts] = (float)(yt.n[a] * q * pi);
+        }
+      }
+      const double nr = pr * x - pi * y;
+      pi = pr * y + pi * x;
+      pr = nr;
+    }
+  }
+}
+
+void launch_rtab_build(float* rtab, int N, int ell_max, const RGeo& g, int nsm, cudaStream_t s) {
+  k_rtab_build<<<8 * nsm, 256, 0, s>>>(rtab, N, ell_max, g, host_ytab<double>());
 }
 
 void launch_ytab_build(float* ytab, int N, int ell_max, int nsm, cudaStream_t s) {

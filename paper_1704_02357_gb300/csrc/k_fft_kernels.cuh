@@ -186,6 +186,7 @@ __global__ void __launch_bounds__(ylm_thread_cap(LT), sizeof(T) == 4 ? ylm_min_b
                                                   int64_t spec_stride, int ell, int h0, int M,
                                                   const ux<T>* __restrict__ twh, const ux<T>* __restrict__ twr,
                                                   const T* __restrict__ axis, int rows,
+                                                  const float* __restrict__ rtab,
                                                   const __grid_constant__ YTab<T> yt) {
   using C = cx<T>;
   using S = ZShape<N, XP>;
@@ -195,9 +196,20 @@ __global__ void __launch_bounds__(ylm_thread_cap(LT), sizeof(T) == 4 ? ylm_min_b
   C* xb = reinterpret_cast<C*>(smraw);
   const int row0 = blockIdx.x * rows;
   const int a_lo = LT < 0 ? 0 : harm_a(h0), a_hi = LT < 0 ? 0 : harm_a(h0 + M - 1);
-  const T sq2 = T(1.41421356237309504880);
   for (int r = 0; r < rows; r++) {
     const int grow = row0 + r;
+    if constexpr (sizeof(T) == 4 && LT >= 0) {
+      if (rtab) {  // Y_lm(rhat) from the table (harmonics h0.., one slot of N^3 nodes each)
+        constexpr int64_t pts = (int64_t)N * N * N;
+        const T* frow = f + (int64_t)grow * N;
+        const float* trow = rtab + (int64_t)grow * N;
+        for (int kk = threadIdx.x; kk < N; kk += blockDim.x) {
+          const T fv = frow[kk];
+          for (int s = 0; s < M; s++) stage[(s * rows + r) * N + kk] = fv * __ldg(trow + s * pts + kk);
+        }
+        continue;
+      }
+    }
     const int i = grow / N, j = grow - i * N;
     const T vx = axis[i], vy = axis[N + j];
     const T* frow = f + (int64_t)grow * N;
@@ -229,13 +241,13 @@ __global__ void __launch_bounds__(ylm_thread_cap(LT), sizeof(T) == 4 ? ylm_min_b
 #pragma unroll
         for (int a = 0; a <= LT; a++) {
           if (a >= a_lo && a <= a_hi) {
-            const T q = fv * ylm_q<T, true>(yt, LT, a, z);
+            const T q = ylm_qt<T, true>(yt, LT, a, z);
             if (a == 0) {
-              stage[r * N + kk] = q;
+              stage[r * N + kk] = fv * ylm_norm(yt, 0, q);
             } else {
               const int hp = 2 * a - 1, hm = 2 * a;
-              if (hp >= h0 && hp < h0 + M) stage[((hp - h0) * rows + r) * N + kk] = sq2 * q * pr;
-              if (hm >= h0 && hm < h0 + M) stage[((hm - h0) * rows + r) * N + kk] = sq2 * q * pi;
+              if (hp >= h0 && hp < h0 + M) stage[((hp - h0) * rows + r) * N + kk] = fv * ylm_norm(yt, a, q * pr);
+              if (hm >= h0 && hm < h0 + M) stage[((hm - h0) * rows + r) * N + kk] = fv * ylm_norm(yt, a, q * pi);
             }
           }
           const T nr = pr * x - pi * y;
@@ -249,13 +261,13 @@ __global__ void __launch_bounds__(ylm_thread_cap(LT), sizeof(T) == 4 ? ylm_min_b
           pr = nr;
         }
         for (int a = a_lo; a <= a_hi; a++) {
-          const T q = fv * ylm_q<T, true>(yt, ell, a, z);
+          const T q = ylm_qt<T, true>(yt, ell, a, z);
           if (a == 0) {
-            stage[r * N + kk] = q;
+            stage[r * N + kk] = fv * ylm_norm(yt, 0, q);
           } else {
             const int hp = 2 * a - 1, hm = 2 * a;
-            if (hp >= h0 && hp < h0 + M) stage[((hp - h0) * rows + r) * N + kk] = sq2 * q * pr;
-            if (hm >= h0 && hm < h0 + M) stage[((hm - h0) * rows + r) * N + kk] = sq2 * q * pi;
+            if (hp >= h0 && hp < h0 + M) stage[((hp - h0) * rows + r) * N + kk] = fv * ylm_norm(yt, a, q * pr);
+            if (hm >= h0 && hm < h0 + M) stage[((hm - h0) * rows + r) * N + kk] = fv * ylm_norm(yt, a, q * pi);
           }
           const T nr = pr * x - pi * y;
           pi = pr * y + pi * x;
@@ -442,7 +454,6 @@ __global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T, Shape<N>::E>(Shape
   wb.b = reinterpret_cast<double*>(sF0 + N * TW);
   wb.w = reinterpret_cast<T*>(wb.b + ba.nk);
   wb.init();
-  const T sq2 = T(1.41421356237309504880);
   const int c = threadIdx.x % TW, t = threadIdx.x / TW;
   constexpr int ntz = NH / TW;
   constexpr int64_t si = (int64_t)N * NH;
@@ -485,7 +496,8 @@ __global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T, Shape<N>::E>(Shape
         } else {
           const T inv = rsqrt_t<T>(r2);
           const T x = fx * inv, y = fy * inv;
-          Y = ylm_q<T>(yt, ell, a, fz * inv);
+          Y = ylm_qt<T>(yt, ell, a, fz * inv);
+          if (a == 0) Y = ylm_norm(yt, 0, Y);
           if (a > 0) {
             T pr = x, pi = y;
             for (int u = 1; u < a; u++) {
@@ -493,7 +505,7 @@ __global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T, Shape<N>::E>(Shape
               pi = pr * y + pi * x;
               pr = nr;
             }
-            Y = sq2 * Y * (sg > 0 ? pr : pi);
+            Y = ylm_norm(yt, a, Y * (sg > 0 ? pr : pi));
           }
         }
         const C fv = sF0[(t + Tc * e) * TW + c];
@@ -687,30 +699,35 @@ template <typename T, int N> struct Passes {
   }
   template <int LT, bool XP>
   static void ylm_z_v(const T* f, C* out, int64_t stride, int ell, int h0, int M, const U* twh, const U* twr,
-                      const T* axis, int rows, cudaStream_t s) {
+                      const T* axis, int rows, const float* rtab, cudaStream_t s) {
     const size_t smem = smem_ylm(M, rows);
     const dim3 grid(N * N / rows), block(M * rows * ZShape<N, XP>::Tz);
     set_smem(k_ylm_r2c_z<T, N, LT, XP>, smem);
-    k_ylm_r2c_z<T, N, LT, XP><<<grid, block, smem, s>>>(f, out, stride, ell, h0, M, twh, twr, axis, rows, host_ytab<T>());
+    k_ylm_r2c_z<T, N, LT, XP><<<grid, block, smem, s>>>(f, out, stride, ell, h0, M, twh, twr, axis, rows, rtab,
+                                                         host_ytab<T>());
   }
   template <bool XP>
   static void ylm_z_x(const T* f, C* out, int64_t stride, int ell, int h0, int M, const U* twh, const U* twr,
-                      const T* axis, int rows, cudaStream_t s) {
+                      const T* axis, int rows, const float* rtab, cudaStream_t s) {
+    if (rtab && ell >= 0) {  // weights from the table: no recurrence to specialise
+      ylm_z_v<0, XP>(f, out, stride, ell, h0, M, twh, twr, axis, rows, rtab, s);
+      return;
+    }
     switch (ell) {  // the headline multipoles get unrolled recurrences
-      case 2: ylm_z_v<2, XP>(f, out, stride, ell, h0, M, twh, twr, axis, rows, s); break;
-      case 4: ylm_z_v<4, XP>(f, out, stride, ell, h0, M, twh, twr, axis, rows, s); break;
+      case 2: ylm_z_v<2, XP>(f, out, stride, ell, h0, M, twh, twr, axis, rows, nullptr, s); break;
+      case 4: ylm_z_v<4, XP>(f, out, stride, ell, h0, M, twh, twr, axis, rows, nullptr, s); break;
       // Cartesian monomials of degree 2 and 4 (h = monomial index)
-      case -2: ylm_z_v<-2, XP>(f, out, stride, ell, h0, M, twh, twr, axis, rows, s); break;
-      case -4: ylm_z_v<-4, XP>(f, out, stride, ell, h0, M, twh, twr, axis, rows, s); break;
-      default: ylm_z_v<0, XP>(f, out, stride, ell, h0, M, twh, twr, axis, rows, s);
+      case -2: ylm_z_v<-2, XP>(f, out, stride, ell, h0, M, twh, twr, axis, rows, nullptr, s); break;
+      case -4: ylm_z_v<-4, XP>(f, out, stride, ell, h0, M, twh, twr, axis, rows, nullptr, s); break;
+      default: ylm_z_v<0, XP>(f, out, stride, ell, h0, M, twh, twr, axis, rows, nullptr, s);
     }
   }
   static void ylm_z(const T* f, C* out, int64_t stride, int ell, int h0, int M, const U* twh, const U* twr,
-                    const T* axis, int rows, int xp, cudaStream_t s) {
+                    const T* axis, int rows, const float* rtab, int xp, cudaStream_t s) {
     if (sizeof(T) == 4 && xp)
-      ylm_z_x<sizeof(T) == 4>(f, out, stride, ell, h0, M, twh, twr, axis, rows, s);
+      ylm_z_x<sizeof(T) == 4>(f, out, stride, ell, h0, M, twh, twr, axis, rows, rtab, s);
     else
-      ylm_z_x<false>(f, out, stride, ell, h0, M, twh, twr, axis, rows, s);
+      ylm_z_x<false>(f, out, stride, ell, h0, M, twh, twr, axis, rows, sizeof(T) == 4 ? rtab : nullptr, s);
   }
   // variant 0: TW columns per block; variant 1: TW/2 (half the threads and shared memory)
   template <int TWV, bool XP>

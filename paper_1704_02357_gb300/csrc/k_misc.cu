@@ -91,12 +91,13 @@ __device__ __forceinline__ PaintArgs resolve(const PaintArgs& in) {
 }
 
 // ------------------------------------------------------------------ a1: weighted catalogs
-// Per-block partials: [0] sum w_c, [1] sum v^2 (v = w_c w_fkp), [2] sum nbar w_c w_fkp^2.
+// Per-block partials: [0] sum w_c, [1] sum v^2 (v = w_c w_fkp), [2] sum nbar w_c w_fkp^2,
+// [3] sum |v| (bounds every mesh value, for the fixed-point scale of the exact paint).
 // Invalid particles are left out here and counted by the paint kernel.
 __global__ void __launch_bounds__(kSumThreads) k_catalog_partials(PaintArgs a_in, double* out) {
   __shared__ double red[kSumThreads / 32];
   const PaintArgs a = resolve(a_in);
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.count;
        p += (int64_t)gridDim.x * blockDim.x) {
     double x, y, z;
@@ -112,16 +113,18 @@ __global__ void __launch_bounds__(kSumThreads) k_catalog_partials(PaintArgs a_in
     s0 += wc;
     s1 += v * v;
     s2 += nb * wc * wf * wf;
+    s3 += fabs(v);
   }
   const double r0 = block_sum(s0, red);
   const double r1 = block_sum(s1, red);
   const double r2 = block_sum(s2, red);
+  const double r3 = block_sum(s3, red);
   if (threadIdx.x == 0) {
     double* o = out + (int64_t)blockIdx.x * kSumVals;
     o[0] = r0;
     o[1] = r1;
     o[2] = r2;
-    o[3] = 0.0;
+    o[3] = r3;
   }
 }
 
@@ -136,18 +139,33 @@ struct Neu {
   __device__ __forceinline__ double val() const { return s + c; }
 };
 
-// One thread adds the block partials in a fixed order: deterministic alpha, I, S.
-__global__ void k_catalog_final(const double* pd, int nbd, const double* pr, int nbr, double* d) {
+// The fixed-point scale 2^S of the exact paint for meshes whose values are all bounded by
+// `bound` in magnitude: every cell sum then stays below 2^61 in units of 2^-S.
+__device__ double fix_scale(double bound) {
+  int e = 0;
+  frexp(bound, &e);  // bound < 2^e
+  int S = bound > 0.0 ? 61 - e : 61;
+  S = S > 100 ? 100 : (S < -100 ? -100 : S);
+  return ldexp(1.0, S);
+}
+
+// One thread adds the block partials in a fixed order: deterministic alpha, I, S. `fix`
+// (nullable) receives the exact paint's fixed-point scale for data (+v) and randoms
+// (-alpha v) painted together.
+__global__ void k_catalog_final(const double* pd, int nbd, const double* pr, int nbr, double* d, double* fix) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   Neu wd, sd, wr, sr, ir;
+  double ad = 0.0, ar = 0.0;
   for (int b = 0; b < nbd; b++) {
     wd.add(pd[b * kSumVals + 0]);
     sd.add(pd[b * kSumVals + 1]);
+    ad += pd[b * kSumVals + 3];
   }
   for (int b = 0; b < nbr; b++) {
     wr.add(pr[b * kSumVals + 0]);
     sr.add(pr[b * kSumVals + 1]);
     ir.add(pr[b * kSumVals + 2]);
+    ar += pr[b * kSumVals + 3];
   }
   const double alpha = wd.val() / wr.val();
   d[D_WD] = wd.val();
@@ -160,6 +178,7 @@ __global__ void k_catalog_final(const double* pd, int nbd, const double* pr, int
   d[D_SD] = sd.val();
   d[D_SR] = sr.val();
   d[D_IR] = ir.val();
+  if (fix) *fix = fix_scale(ad + fabs(alpha) * ar);
 }
 
 // Unit completeness weights and one n̄: W = counts, v = w_fkp for every particle.
@@ -178,6 +197,7 @@ __global__ void k_derive_uniform(int64_t nd, int64_t nr, double wf, double nbar,
   d[D_SD] = sd;
   d[D_SR] = sr;
   d[D_IR] = ir;
+  d[D_FIX] = fix_scale(fabs(wf) * (Wd + alpha * Wr));
 }
 
 void launch_catalog_partials(const PaintArgs& a, double* partials, int nblocks, cudaStream_t s) {
@@ -185,8 +205,8 @@ void launch_catalog_partials(const PaintArgs& a, double* partials, int nblocks, 
 }
 
 void launch_catalog_final(const double* part_d, int nb_d, const double* part_r, int nb_r, double* derived,
-                          cudaStream_t s) {
-  k_catalog_final<<<1, 32, 0, s>>>(part_d, nb_d, part_r, nb_r, derived);
+                          cudaStream_t s, double* fix) {
+  k_catalog_final<<<1, 32, 0, s>>>(part_d, nb_d, part_r, nb_r, derived, fix);
 }
 
 void launch_derive_uniform(int64_t n_d, int64_t n_r, double wf, double nbar, double* derived, cudaStream_t s) {
@@ -362,18 +382,43 @@ template void launch_paint<double>(const PaintArgs&, int, int, int, double*, dou
                                    cudaStream_t);
 
 // ------------------------------------------------------------------ a2: tile-binned painting
-// FP32 meshes. Particles of both catalogs are counting-sorted by the 16^3-cell tile that
-// holds their (mesh 1) base node; one block per non-empty tile then accumulates the tile and
-// a 2-cell halo in shared memory (both interlaced meshes) and adds it into the global meshes
-// once. Per particle the 24-bit fixed-point grid coordinate is kept as a record
-// {(cell in tile << 24) | fraction, x3; value}.
-constexpr int kPT = 16;             // tile side (cells)
-constexpr int kPH = 2;              // halo on each side
-constexpr int kPS = kPT + 2 * kPH;  // shared tile side
-constexpr int kPS3 = kPS * kPS * kPS;
+// FP32 meshes, accumulated exactly. One block per 16^3-cell tile owns its cells: it sums every
+// contribution that lands in them as a 64-bit fixed-point integer (units 2^-S, S from the
+// catalogs' sum of |v| so that no sum can overflow) and stores each cell once, rounded to FP32.
+// Integer sums do not depend on the order of the additions, so the meshes are the exact sums of
+// the particles' FP32 contributions, rounded once, identical from run to run. With FP32 atomics
+// instead, each run adds in another order, and the rounding of the many small randoms
+// contributions left an order-dependent error on the survey window's largest-scale modes large
+// enough to move a 3%-of-P_0 quadrupole in the first k bin by ~1e-5.
+//
+// A particle whose footprint (both interlaced meshes) crosses a tile face is listed for every
+// tile it touches: per axis the footprint spans at most 4 cells, so at most 2 tiles per axis.
+// Record: per axis the grid coordinate relative to the origin of the particle's first tile,
+// in 2^-24 cells (29 bits), with bit 31 set when the footprint reaches the next tile; in the
+// tile-sorted copy bit 29 says the record sits in that next tile (coordinate 16 cells less).
+constexpr int kPT = 16;  // tile side (cells)
+constexpr int kPT3 = kPT * kPT * kPT;
 constexpr unsigned kNoTile = 0xffffffffu;
+constexpr unsigned kCoordMask = (1u << 29) - 1u;
+constexpr unsigned kSpan2 = 1u << 31;
+constexpr unsigned kNextTile = 1u << 29;
 
-template <int WIN>
+// Lowest and highest footprint cell along one axis (unwrapped), both meshes.
+template <int WIN, bool INTER>
+__device__ __forceinline__ void footprint(int64_t U, int64_t& lo, int64_t& hi) {
+  if (WIN == PSPEC_WINDOW_CIC) {
+    const int64_t c1 = U >> 24;
+    lo = INTER ? ((U - (1ll << 23)) >> 24) : c1;
+    hi = c1 + 1;
+  } else {
+    const int64_t c1 = (U + (1ll << 23)) >> 24;  // floor(u + 1/2)
+    const int64_t c2 = U >> 24;                   // centre of the mesh painted at u - 1/2
+    lo = (INTER ? (c1 < c2 ? c1 : c2) : c1) - 1;
+    hi = (INTER ? (c1 > c2 ? c1 : c2) : c1) + 1;
+  }
+}
+
+template <int WIN, bool INTER>
 __global__ void __launch_bounds__(256) k_ptile_prep(PaintArgs a_in, int is_randoms, double* __restrict__ derived,
                                                     TileArgs ta, int64_t offset, int N) {
   const PaintArgs a = resolve(a_in);
@@ -404,21 +449,26 @@ __global__ void __launch_bounds__(256) k_ptile_prep(PaintArgs a_in, int is_rando
     if (u[0] < 0.0 || u[0] >= lim || u[1] < 0.0 || u[1] >= lim || u[2] < 0.0 || u[2] >= lim) out++;
     const float v = dither_pick(uniform ? d_uniform : dither_of(sign * wc * fkp_w(a, nb)), p, is_randoms);
     unsigned packed[3];
-    int tc[3];
+    int tb[3], span[3];
     for (int d = 0; d < 3; d++) {
       const int64_t U = __double2ll_rn(u[d] * 16777216.0);
-      // base node of mesh 1: floor(u) (CIC) or floor(u + 1/2) (TSC); fraction relative to
-      // that node (CIC) or to that node - 1/2 (TSC), in [0, 2^24)
-      const int64_t c = WIN == PSPEC_WINDOW_CIC ? (U >> 24) : ((U + (1ll << 23)) >> 24);
-      const unsigned f = (unsigned)(U - c * 16777216ll + (WIN == PSPEC_WINDOW_CIC ? 0 : (1ll << 23)));
-      const int cw = wrap(c, N);
-      tc[d] = cw / kPT;
-      packed[d] = ((unsigned)(cw - tc[d] * kPT) << 24) | f;
+      int64_t lo, hi;
+      footprint<WIN, INTER>(U, lo, hi);
+      const int low = wrap(lo, N);  // the footprint's first cell, wrapped; U shifted by the same period
+      tb[d] = low / kPT;
+      const int64_t rel = U - (lo - low + (int64_t)tb[d] * kPT) * 16777216ll;  // in [0, 19 cells)
+      span[d] = (low - tb[d] * kPT) + (int)(hi - lo) >= kPT ? 2 : 1;
+      packed[d] = (unsigned)rel | (span[d] == 2 ? kSpan2 : 0u);
     }
-    const unsigned tile = (unsigned)((tc[0] * nts + tc[1]) * nts + tc[2]);
+    const unsigned tile = (unsigned)((tb[0] * nts + tb[1]) * nts + tb[2]);
     ta.rec[offset + p] = make_uint4(packed[0], packed[1], packed[2], __float_as_uint(v));
     ta.tile_of[offset + p] = tile;
-    atomicAdd(&ta.cnt[tile], 1u);
+    for (int dx = 0; dx < span[0]; dx++)
+      for (int dy = 0; dy < span[1]; dy++)
+        for (int dz = 0; dz < span[2]; dz++) {
+          const int t = ((((tb[0] + dx) % nts) * nts + (tb[1] + dy) % nts) * nts) + (tb[2] + dz) % nts;
+          atomicAdd(&ta.cnt[t], 1u);
+        }
   }
   const unsigned nb_w = __reduce_add_sync(0xffffffffu, bad);
   const unsigned no_w = __reduce_add_sync(0xffffffffu, out);
@@ -451,18 +501,32 @@ __global__ void __launch_bounds__(1024) k_ptile_scan(TileArgs ta, int ntiles) {
   }
 }
 
-__global__ void __launch_bounds__(256) k_ptile_scatter(TileArgs ta, int64_t total, const DevCat* dc, const int* cur) {
+// Each record goes to every tile its footprint touches (the order within a tile is free: the
+// tile's sums are exact).
+__global__ void __launch_bounds__(256) k_ptile_scatter(TileArgs ta, int64_t total, const DevCat* dc, const int* cur,
+                                                       int N) {
   if (dc) total = dc[*cur].count;
+  const int nts = N / kPT;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += (int64_t)gridDim.x * blockDim.x) {
     const unsigned t = ta.tile_of[p];
     if (t == kNoTile) continue;
-    const unsigned pos = atomicAdd(&ta.cursor[t], 1u);
-    ta.sorted[pos] = ta.rec[p];
+    const uint4 r = ta.rec[p];
+    const int tb[3] = {(int)(t / (nts * nts)), (int)((t / nts) % nts), (int)(t % nts)};
+    const int sx = (r.x & kSpan2) ? 2 : 1, sy = (r.y & kSpan2) ? 2 : 1, sz = (r.z & kSpan2) ? 2 : 1;
+    for (int dx = 0; dx < sx; dx++)
+      for (int dy = 0; dy < sy; dy++)
+        for (int dz = 0; dz < sz; dz++) {
+          const int tt = ((((tb[0] + dx) % nts) * nts + (tb[1] + dy) % nts) * nts) + (tb[2] + dz) % nts;
+          const unsigned pos = atomicAdd(&ta.cursor[tt], 1u);
+          ta.sorted[pos] = make_uint4((r.x & kCoordMask) | (dx ? kNextTile : 0u),
+                                      (r.y & kCoordMask) | (dy ? kNextTile : 0u),
+                                      (r.z & kCoordMask) | (dz ? kNextTile : 0u), r.w);
+        }
   }
 }
 
-// Tile-local node indices (0 .. kPS-1) and weights along one axis from the tile-local
-// fixed-point coordinate V (2^24 per cell; V = 0 at the tile's first cell).
+// Tile-local node indices (may fall outside [0, kPT): not this tile's) and weights along one
+// axis from the tile-local grid coordinate V (2^24 per cell).
 template <int WIN>
 __device__ __forceinline__ void tile_nodes(int V, int* idx, float* w) {
   if (WIN == PSPEC_WINDOW_CIC) {
@@ -470,152 +534,171 @@ __device__ __forceinline__ void tile_nodes(int V, int* idx, float* w) {
     const float d = (float)(V - c * 16777216) * 5.9604644775390625e-8f;
     w[0] = 1.f - d;
     w[1] = d;
-    idx[0] = c + kPH;
-    idx[1] = c + 1 + kPH;
+    idx[0] = c;
+    idx[1] = c + 1;
   } else {
     const int c = (V + (1 << 23)) >> 24;
     const float d = (float)(V - c * 16777216) * 5.9604644775390625e-8f;
     w[0] = 0.5f * (0.5f - d) * (0.5f - d);
     w[1] = 0.75f - d * d;
     w[2] = 0.5f * (0.5f + d) * (0.5f + d);
-    idx[0] = c - 1 + kPH;
-    idx[1] = c + kPH;
-    idx[2] = c + 1 + kPH;
+    idx[0] = c - 1;
+    idx[1] = c;
+    idx[2] = c + 1;
   }
 }
 
+__device__ __forceinline__ bool in_tile(int i) { return (unsigned)i < (unsigned)kPT; }
+
+// The contribution v wx wy wz (FP32, rounded as the direct paint rounds it) in units of 2^-S.
 template <int WIN>
-__device__ __forceinline__ void tile_scatter(float* st, const int (&ix)[3], const int (&iy)[3], const int (&iz)[3],
-                                             const float (&wx)[3], const float (&wy)[3], const float (&wz)[3],
-                                             float v) {
+__device__ __forceinline__ void tile_scatter(unsigned long long* acc, const int (&ix)[3], const int (&iy)[3],
+                                             const int (&iz)[3], const float (&wx)[3], const float (&wy)[3],
+                                             const float (&wz)[3], float v, float scale) {
   constexpr int K = WIN == PSPEC_WINDOW_CIC ? 2 : 3;
 #pragma unroll
   for (int a = 0; a < K; a++) {
+    if (!in_tile(ix[a])) continue;
     const float va = v * wx[a];
 #pragma unroll
     for (int b = 0; b < K; b++) {
+      if (!in_tile(iy[b])) continue;
       const float vb = va * wy[b];
-      float* row = st + (ix[a] * kPS + iy[b]) * kPS;
+      unsigned long long* row = acc + (ix[a] * kPT + iy[b]) * kPT;
 #pragma unroll
-      for (int c = 0; c < K; c++) atomicAdd(row + iz[c], vb * wz[c]);
+      for (int c = 0; c < K; c++) {
+        if (!in_tile(iz[c])) continue;
+        const long long q = __float2ll_rn((vb * wz[c]) * scale);
+        atomicAdd(row + iz[c], (unsigned long long)q);
+      }
     }
   }
 }
 
+// One block per tile (every tile, so that empty tiles store their zeros): sums its records into
+// shared 64-bit accumulators, then stores each cell of the tile once.
 template <int WIN, bool INTER>
 __global__ void __launch_bounds__(256) k_ptile_paint(TileArgs ta, float* __restrict__ m1, float* __restrict__ m2,
-                                                     int N) {
-  extern __shared__ float st[];  // [INTER ? 2 : 1][kPS^3]
+                                                     int N, const double* __restrict__ fix) {
+  extern __shared__ unsigned long long acc[];  // [INTER ? 2 : 1][kPT^3]
+  constexpr int NM = INTER ? 2 : 1;
   const int tile = blockIdx.x;
   const unsigned n = ta.cnt[tile];
-  if (n == 0) return;
   const unsigned o = ta.off[tile];
-  constexpr int NM = INTER ? 2 : 1;
-  for (int i = threadIdx.x; i < NM * kPS3; i += blockDim.x) st[i] = 0.f;
+  const double sc = *fix;
+  const float scale = (float)sc, inv = (float)(1.0 / sc);  // powers of two: exact
+  for (int i = threadIdx.x; i < NM * kPT3; i += blockDim.x) acc[i] = 0ull;
   __syncthreads();
   for (unsigned q = threadIdx.x; q < n; q += blockDim.x) {
     const uint4 r = ta.sorted[o + q];
     const float v = __uint_as_float(r.w);
-    // tile-local fixed-point coordinate of the particle (mesh 1)
-    const int off1 = WIN == PSPEC_WINDOW_CIC ? 0 : (1 << 23);
-    const int V[3] = {(int)((r.x >> 24) << 24) + (int)(r.x & 0xffffffu) - off1,
-                      (int)((r.y >> 24) << 24) + (int)(r.y & 0xffffffu) - off1,
-                      (int)((r.z >> 24) << 24) + (int)(r.z & 0xffffffu) - off1};
+    const int V[3] = {(int)(r.x & kCoordMask) - ((r.x & kNextTile) ? (kPT << 24) : 0),
+                      (int)(r.y & kCoordMask) - ((r.y & kNextTile) ? (kPT << 24) : 0),
+                      (int)(r.z & kCoordMask) - ((r.z & kNextTile) ? (kPT << 24) : 0)};
     int ix[3], iy[3], iz[3];
     float wx[3], wy[3], wz[3];
     tile_nodes<WIN>(V[0], ix, wx);
     tile_nodes<WIN>(V[1], iy, wy);
     tile_nodes<WIN>(V[2], iz, wz);
-    tile_scatter<WIN>(st, ix, iy, iz, wx, wy, wz, v);
+    tile_scatter<WIN>(acc, ix, iy, iz, wx, wy, wz, v, scale);
     if (INTER) {
       const int h = 1 << 23;  // half a cell
       tile_nodes<WIN>(V[0] - h, ix, wx);
       tile_nodes<WIN>(V[1] - h, iy, wy);
       tile_nodes<WIN>(V[2] - h, iz, wz);
-      tile_scatter<WIN>(st + kPS3, ix, iy, iz, wx, wy, wz, v);
+      tile_scatter<WIN>(acc + kPT3, ix, iy, iz, wx, wy, wz, v, scale);
     }
   }
   __syncthreads();
   const int nts = N / kPT;
   const int tz = tile % nts, ty = (tile / nts) % nts, tx = tile / (nts * nts);
-  const int gx0 = tx * kPT - kPH, gy0 = ty * kPT - kPH, gz0 = tz * kPT - kPH;
-  for (int i = threadIdx.x; i < NM * kPS3; i += blockDim.x) {
-    const float val = st[i];
-    if (val == 0.f) continue;
-    const int mesh = i / kPS3, cell = i - mesh * kPS3;
-    const int lx = cell / (kPS * kPS), ly = (cell / kPS) % kPS, lz = cell % kPS;
-    const int gx = wrap(gx0 + lx, N), gy = wrap(gy0 + ly, N), gz = wrap(gz0 + lz, N);
-    float* m = mesh ? m2 : m1;
-    atomicAdd(m + ((int64_t)gx * N + gy) * N + gz, val);
+  for (int i = threadIdx.x; i < NM * kPT3; i += blockDim.x) {
+    const int mesh = i / kPT3, cell = i - mesh * kPT3;
+    const int lx = cell / (kPT * kPT), ly = (cell / kPT) % kPT, lz = cell % kPT;
+    const int64_t g = ((int64_t)(tx * kPT + lx) * N + (ty * kPT + ly)) * N + tz * kPT + lz;
+    (mesh ? m2 : m1)[g] = __ll2float_rn((long long)acc[i]) * inv;
   }
 }
 
-void launch_ptile_prep(const PaintArgs& a, int window, int is_randoms, double* derived, const TileArgs& ta,
-                       int64_t offset, int N, int nblocks, cudaStream_t s) {
+void launch_ptile_prep(const PaintArgs& a, int window, int interlaced, int is_randoms, double* derived,
+                       const TileArgs& ta, int64_t offset, int N, int nblocks, cudaStream_t s) {
   if (!a.dc && a.count <= 0) return;
   const int64_t need = a.dc ? nblocks : (a.count + 255) / 256;
   const int nb = (int)(need < nblocks ? need : nblocks);
-  if (window == PSPEC_WINDOW_CIC)
-    k_ptile_prep<PSPEC_WINDOW_CIC><<<nb, 256, 0, s>>>(a, is_randoms, derived, ta, offset, N);
-  else
-    k_ptile_prep<PSPEC_WINDOW_TSC><<<nb, 256, 0, s>>>(a, is_randoms, derived, ta, offset, N);
+  if (window == PSPEC_WINDOW_CIC) {
+    if (interlaced)
+      k_ptile_prep<PSPEC_WINDOW_CIC, true><<<nb, 256, 0, s>>>(a, is_randoms, derived, ta, offset, N);
+    else
+      k_ptile_prep<PSPEC_WINDOW_CIC, false><<<nb, 256, 0, s>>>(a, is_randoms, derived, ta, offset, N);
+  } else {
+    if (interlaced)
+      k_ptile_prep<PSPEC_WINDOW_TSC, true><<<nb, 256, 0, s>>>(a, is_randoms, derived, ta, offset, N);
+    else
+      k_ptile_prep<PSPEC_WINDOW_TSC, false><<<nb, 256, 0, s>>>(a, is_randoms, derived, ta, offset, N);
+  }
 }
 
 void launch_ptile_scan(const TileArgs& ta, int ntiles, cudaStream_t s) { k_ptile_scan<<<1, 1024, 0, s>>>(ta, ntiles); }
 
-void launch_ptile_scatter(const TileArgs& ta, int64_t total, const DevCat* dc, const int* cur, int nblocks,
+void launch_ptile_scatter(const TileArgs& ta, int64_t total, const DevCat* dc, const int* cur, int N, int nblocks,
                           cudaStream_t s) {
   if (!dc && total <= 0) return;
   const int64_t need = dc ? nblocks : (total + 255) / 256;
   const int nb = (int)(need < nblocks ? need : nblocks);
-  k_ptile_scatter<<<nb, 256, 0, s>>>(ta, total, dc, cur);
+  k_ptile_scatter<<<nb, 256, 0, s>>>(ta, total, dc, cur, N);
 }
 
 template <typename K> static void set_smem_attr(K kernel, size_t bytes) {
   if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-void launch_ptile_paint(const TileArgs& ta, int window, int interlaced, float* m1, float* m2, int N, cudaStream_t s) {
+void launch_ptile_paint(const TileArgs& ta, int window, int interlaced, float* m1, float* m2, int N,
+                        const double* fix, cudaStream_t s) {
   const int ntiles = (N / kPT) * (N / kPT) * (N / kPT);
-  const size_t smem = (size_t)(interlaced ? 2 : 1) * kPS3 * sizeof(float);
+  const size_t smem = (size_t)(interlaced ? 2 : 1) * kPT3 * sizeof(unsigned long long);
   if (window == PSPEC_WINDOW_CIC) {
     if (interlaced) {
       set_smem_attr(k_ptile_paint<PSPEC_WINDOW_CIC, true>, smem);
-      k_ptile_paint<PSPEC_WINDOW_CIC, true><<<ntiles, 256, smem, s>>>(ta, m1, m2, N);
+      k_ptile_paint<PSPEC_WINDOW_CIC, true><<<ntiles, 256, smem, s>>>(ta, m1, m2, N, fix);
     } else {
-      k_ptile_paint<PSPEC_WINDOW_CIC, false><<<ntiles, 256, smem, s>>>(ta, m1, m2, N);
+      k_ptile_paint<PSPEC_WINDOW_CIC, false><<<ntiles, 256, smem, s>>>(ta, m1, m2, N, fix);
     }
   } else {
     if (interlaced) {
       set_smem_attr(k_ptile_paint<PSPEC_WINDOW_TSC, true>, smem);
-      k_ptile_paint<PSPEC_WINDOW_TSC, true><<<ntiles, 256, smem, s>>>(ta, m1, m2, N);
+      k_ptile_paint<PSPEC_WINDOW_TSC, true><<<ntiles, 256, smem, s>>>(ta, m1, m2, N, fix);
     } else {
-      k_ptile_paint<PSPEC_WINDOW_TSC, false><<<ntiles, 256, smem, s>>>(ta, m1, m2, N);
+      k_ptile_paint<PSPEC_WINDOW_TSC, false><<<ntiles, 256, smem, s>>>(ta, m1, m2, N, fix);
     }
   }
 }
 
 // ------------------------------------------------------------------ batched mocks
-// rsums = (W_r, S_r, I_r) of the cached randoms.
+// rsums = (W_r, S_r, I_r, fixed-point scale of the randoms mesh painted alone) of the cached randoms.
 __global__ void k_randoms_sums(const double* pr, int nbr, double* rsums) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   Neu wr, sr, ir;
+  double ar = 0.0;
   for (int b = 0; b < nbr; b++) {
     wr.add(pr[b * kSumVals + 0]);
     sr.add(pr[b * kSumVals + 1]);
     ir.add(pr[b * kSumVals + 2]);
+    ar += pr[b * kSumVals + 3];
   }
   rsums[0] = wr.val();
   rsums[1] = sr.val();
   rsums[2] = ir.val();
+  rsums[3] = fix_scale(ar);
 }
 
 __global__ void k_catalog_final_cached(const double* pd, int nbd, const double* rsums, double* d) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   Neu wd, sd;
+  double ad = 0.0;
   for (int b = 0; b < nbd; b++) {
     wd.add(pd[b * kSumVals + 0]);
     sd.add(pd[b * kSumVals + 1]);
+    ad += pd[b * kSumVals + 3];
   }
   const double Wr = rsums[0], Sr = rsums[1], Ir = rsums[2];
   const double alpha = wd.val() / Wr;
@@ -629,6 +712,7 @@ __global__ void k_catalog_final_cached(const double* pd, int nbd, const double* 
   d[D_SD] = sd.val();
   d[D_SR] = Sr;
   d[D_IR] = Ir;
+  d[D_FIX] = fix_scale(ad);  // the mock's data mesh is painted alone
 }
 
 template <typename T>

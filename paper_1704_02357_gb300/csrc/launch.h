@@ -16,8 +16,10 @@ struct Geo {
 // Slots of the FP64 bin sums: [slot][kbin].
 enum { SLOT_P0 = 0, SLOT_ELL0 = 1 };
 // Layout of the derived catalog quantities (device doubles).
-enum { D_WD = 0, D_WR, D_ALPHA, D_I, D_S, D_NONFINITE, D_WRAPPED, D_SD, D_SR, D_IR, D_COUNT = 16 };
-constexpr int kSumVals = 4;  // per-block partial: w_c, v^2, nbar w_c w_fkp^2, spare
+// D_FIX: the fixed-point scale 2^S of the exact (tile-binned) paint for the catalogs painted
+// together by pspec_paint (or a mock's data alone).
+enum { D_WD = 0, D_WR, D_ALPHA, D_I, D_S, D_NONFINITE, D_WRAPPED, D_SD, D_SR, D_IR, D_FIX, D_COUNT = 16 };
+constexpr int kSumVals = 4;  // per-block partial: w_c, v^2, nbar w_c w_fkp^2, |v|
 
 // A catalog as a device-side descriptor (batched mocks: the kernels of one captured graph
 // read the current mock's catalog from a table indexed by a device counter).
@@ -60,8 +62,9 @@ struct BinArgs {
 // a1: per-block partial sums of one weighted catalog; final combine into `derived`.
 // When neither catalog carries weight or nbar arrays the closed forms are used instead.
 void launch_catalog_partials(const PaintArgs& a, double* partials, int nblocks, cudaStream_t s);
+// `fix` (nullable): where to store the exact paint's fixed-point scale for both catalogs.
 void launch_catalog_final(const double* part_d, int nb_d, const double* part_r, int nb_r, double* derived,
-                          cudaStream_t s);
+                          cudaStream_t s, double* fix = nullptr);
 void launch_derive_uniform(int64_t n_d, int64_t n_r, double wf, double nbar, double* derived, cudaStream_t s);
 
 // Batched mocks: randoms sums kept from pspec_set_randoms (W_r, S_r, I_r), the data sums of
@@ -81,23 +84,28 @@ template <typename T>
 void launch_paint(const PaintArgs& a, int window, int interlaced, int is_randoms, double* derived, T* mesh1,
                   T* mesh2, int N, int nblocks, cudaStream_t s);
 
-// a2, tile-binned (FP32 meshes): prep (records + tile counts) per catalog, scan, scatter
-// into tile order, then one block per non-empty 16^3 tile. Tile side kPaintTile divides N.
+// a2, tile-binned (FP32 meshes), exact: prep (records + per-tile counts, a particle counted for
+// every 16^3 tile its footprint touches) per catalog, scan, scatter into tile order, then one
+// block per tile sums its cells in 64-bit fixed point (scale 2^S at `fix`) and stores every
+// cell of the tile once (no mesh clearing needed). Tile side kPaintTile divides N. The sorted
+// copy holds up to 8 records per particle (kPaintRecordsMax).
 constexpr int kPaintTile = 16;
+constexpr int kPaintRecordsMax = 8;
 struct TileArgs {
-  unsigned* cnt;     // [ntiles] particles per tile (cleared before prep)
+  unsigned* cnt;     // [ntiles] records per tile (cleared before prep)
   unsigned* off;     // [ntiles] exclusive prefix of cnt
   unsigned* cursor;  // [ntiles] scatter cursors
   uint4* rec;        // [particles] records in input order
-  unsigned* tile_of; // [particles] tile of each record (all ones: left out)
-  uint4* sorted;     // [particles] records in tile order
+  unsigned* tile_of; // [particles] first tile of each record (all ones: left out)
+  uint4* sorted;     // [kPaintRecordsMax * particles] records in tile order
 };
-void launch_ptile_prep(const PaintArgs& a, int window, int is_randoms, double* derived, const TileArgs& ta,
-                       int64_t offset, int N, int nblocks, cudaStream_t s);
+void launch_ptile_prep(const PaintArgs& a, int window, int interlaced, int is_randoms, double* derived,
+                       const TileArgs& ta, int64_t offset, int N, int nblocks, cudaStream_t s);
 void launch_ptile_scan(const TileArgs& ta, int ntiles, cudaStream_t s);
-void launch_ptile_scatter(const TileArgs& ta, int64_t total, const DevCat* dc, const int* cur, int nblocks,
+void launch_ptile_scatter(const TileArgs& ta, int64_t total, const DevCat* dc, const int* cur, int N, int nblocks,
                           cudaStream_t s);
-void launch_ptile_paint(const TileArgs& ta, int window, int interlaced, float* m1, float* m2, int N, cudaStream_t s);
+void launch_ptile_paint(const TileArgs& ta, int window, int interlaced, float* m1, float* m2, int N,
+                        const double* fix, cudaStream_t s);
 
 // Transform passes, one table of launchers per supported mesh side N (pass_*.cu).
 // Tables: tw_half (L = N/2), tw_full (L = N), twr (exp(-2 pi i k/N), k < N/2).
@@ -144,6 +152,15 @@ __host__ __device__ constexpr int ytab_base(int ell) {
   return b;
 }
 void launch_ytab_build(float* ytab, int N, int ell_max, int nsm, cudaStream_t s);
+// Y_lm(rhat) of every mesh node for the Y-weighted z pass (FP32 contexts): the same harmonic
+// slots as the Y_lm(khat) table, every slot one value per node [i][j][k], built in FP64 and
+// rounded once. Evaluated in FP32 per node instead, the weights carry errors that are coherent
+// over the sphere (position rounding, the recurrence and the complex power); through them the
+// shot noise leaks into P_l, ~1e-4 of P_14 and ~2e-5 of a small P_4 at 512^3.
+struct RGeo {
+  double corner[3], H, observer[3];
+};
+void launch_rtab_build(float* rtab, int N, int ell_max, const RGeo& g, int nsm, cudaStream_t s);
 // Cartesian k-space factors mult_q khat^q of every stored mode, q = 0..20 (kCartItems slots).
 void launch_ctab_build(float* ctab, int N, int nsm, cudaStream_t s);
 
@@ -154,8 +171,9 @@ template <typename T> struct PassTable {
   int tz_xp;  // threads per row of the exact-add z passes
   void (*r2c_z)(const T*, cx<T>*, const ux<T>*, const ux<T>*, cudaStream_t);
   void (*c2r_z)(const cx<T>*, T*, const ux<T>*, const ux<T>*, T, int, cudaStream_t);
-  void (*ylm_z)(const T*, cx<T>*, int64_t, int, int, int, const ux<T>*, const ux<T>*, const T*, int, int,
-                cudaStream_t);
+  // ..., rows, Y_lm(rhat) table slot of the group's first harmonic (FP32) or nullptr, xp
+  void (*ylm_z)(const T*, cx<T>*, int64_t, int, int, int, const ux<T>*, const ux<T>*, const T*, int, const float*,
+                int, cudaStream_t);
   size_t (*smem_ylm)(int, int);
   // ..., dir, tile variant, n2_cut (outputs with ny^2 + kz^2 >= n2_cut are not stored), xp
   void (*fft_y)(cx<T>*, int64_t, int, const ux<T>*, int, int, int, int, cudaStream_t);

@@ -53,8 +53,8 @@ struct Plan {
   size_t Sr, Sc;
   int n2max;
   // workspace offsets
-  bool has_ytab = false, has_ctab = false;
-  size_t ytab_bytes = 0, o_ytab = 0, ctab_bytes = 0, o_ctab = 0;
+  bool has_ytab = false, has_ctab = false, has_rtab = false;
+  size_t ytab_bytes = 0, o_ytab = 0, ctab_bytes = 0, o_ctab = 0, rtab_bytes = 0, o_rtab = 0;
   size_t o_xtiles;  // x-pass tiles (j, kz-tile) of the binning pass that hold a binned mode, in order
   size_t o_mesh1, o_mesh2, o_f0, o_w, o_f, o_g, o_twh, o_twf, o_twr, o_axis, o_phase, o_invw, o_bin, o_kmag, o_cnt,
       o_lo, o_hi, o_nmodes, o_ksum, o_sums, o_derived, o_bins, o_out, o_tcnt, o_toff, o_tcur, o_prec, o_ptile,
@@ -117,6 +117,9 @@ pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl,
   // binned with Y_lm evaluated in the kernel)
   pl->ytab_bytes = (size_t)N * N * NH * sizeof(float) * (size_t)ytab_base((p->ell_max & ~1) + 2);
   pl->has_ytab = !f64 && p->ell_max >= 2 && p->ylm_table == 0 && pl->ytab_bytes <= (size_t)PSPEC_YLM_TABLE_AUTO_MAX;
+  // Y_lm(rhat) of every node for the z pass (even l = 2..l_max), twice the k-space table's size
+  pl->rtab_bytes = (size_t)N * N * N * sizeof(float) * (size_t)ytab_base((p->ell_max & ~1) + 2);
+  pl->has_rtab = !f64 && p->ell_max >= 2 && p->ylm_table == 0 && pl->rtab_bytes <= (size_t)PSPEC_YLM_RTABLE_AUTO_MAX;
   {
     size_t need = f64 ? std::max(pl->td->smem_bin(max_kbins), pl->td->smem_combine(max_kbins))
                       : std::max(pl->tf->smem_bin(max_kbins), pl->tf->smem_combine(max_kbins));
@@ -153,6 +156,7 @@ pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl,
   pl->o_phase = take(3 * (size_t)N * usz);
   pl->o_invw = take((N + NH) * csz);
   pl->o_ytab = pl->has_ytab ? take(pl->ytab_bytes) : 0;
+  pl->o_rtab = pl->has_rtab ? take(pl->rtab_bytes) : 0;
   pl->has_ctab = !f64 && p->cartesian == 1;
   pl->ctab_bytes = pl->has_ctab ? (size_t)N * N * NH * sizeof(float) * kCartItems : 0;
   pl->o_ctab = pl->has_ctab ? take(pl->ctab_bytes) : 0;
@@ -176,7 +180,7 @@ pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl,
     pl->o_tcur = take((size_t)pl->ntiles * sizeof(unsigned));
     pl->o_prec = take((size_t)pl->max_particles * 16);
     pl->o_ptile = take((size_t)pl->max_particles * sizeof(unsigned));
-    pl->o_psort = take((size_t)pl->max_particles * 16);
+    pl->o_psort = take((size_t)pl->max_particles * kPaintRecordsMax * 16);
   }
   pl->cache_randoms = p->cache_randoms != 0;
   if (pl->cache_randoms) {
@@ -344,6 +348,15 @@ pspec_status upload_tables(Ctx* c) {
   TRY(run(c, PSPEC_K_OTHER, 0.0, [&] { launch_mode_counts(pl.g, c->at<uint32_t>(pl.o_cnt), c->nsm, c->stream); }));
   if (pl.has_ytab)
     TRY(run(c, PSPEC_K_OTHER, 0.0, [&] { launch_ytab_build(c->at<float>(pl.o_ytab), N, c->p.ell_max, c->nsm, c->stream); }));
+  if (pl.has_rtab) {
+    RGeo g;
+    for (int d = 0; d < 3; d++) {
+      g.corner[d] = c->p.box_corner[d];
+      g.observer[d] = c->p.observer[d];
+    }
+    g.H = H;
+    TRY(run(c, PSPEC_K_OTHER, 0.0, [&] { launch_rtab_build(c->at<float>(pl.o_rtab), N, c->p.ell_max, g, c->nsm, c->stream); }));
+  }
   if (pl.has_ctab)
     TRY(run(c, PSPEC_K_OTHER, 0.0, [&] { launch_ctab_build(c->at<float>(pl.o_ctab), N, c->nsm, c->stream); }));
   e = cudaStreamSynchronize(c->stream);
@@ -459,15 +472,25 @@ double cat_bytes(const pspec_catalog* cat) {
   return per * (double)cat->count;
 }
 
+TileArgs tile_args(Ctx* c) {
+  const Plan& pl = c->pl;
+  TileArgs ta;
+  ta.cnt = c->at<unsigned>(pl.o_tcnt);
+  ta.off = c->at<unsigned>(pl.o_toff);
+  ta.cursor = c->at<unsigned>(pl.o_tcur);
+  ta.rec = c->at<uint4>(pl.o_prec);
+  ta.tile_of = c->at<unsigned>(pl.o_ptile);
+  ta.sorted = c->at<uint4>(pl.o_psort);
+  return ta;
+}
+
 template <typename T>
 pspec_status do_paint(Ctx* c, const pspec_catalog* d, const pspec_catalog* r) {
   const Plan& pl = c->pl;
   const int N = pl.g.N;
   T* m1 = c->at<T>(pl.o_mesh1);
   T* m2 = c->p.interlaced ? c->at<T>(pl.o_mesh2) : nullptr;
-  cudaError_t e = cudaMemsetAsync(m1, 0, pl.Sr, c->stream);
-  if (e == cudaSuccess && m2) e = cudaMemsetAsync(m2, 0, pl.Sr, c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "mesh clear");
+  cudaError_t e = cudaSuccess;
   double* der = c->at<double>(pl.o_derived);
   const PaintArgs ad = paint_args(c, d), ar = paint_args(c, r);
   const bool uniform = !d->weight && !d->nbar && !r->weight && !r->nbar;
@@ -482,7 +505,9 @@ pspec_status do_paint(Ctx* c, const pspec_catalog* d, const pspec_catalog* r) {
     double* part_r = sums + (size_t)pl.nblk_sum * kSumVals;
     TRY(run(c, PSPEC_K_SUMS, cat_bytes(d), [&] { launch_catalog_partials(ad, part_d, pl.nblk_sum, c->stream); }));
     TRY(run(c, PSPEC_K_SUMS, cat_bytes(r), [&] { launch_catalog_partials(ar, part_r, pl.nblk_sum, c->stream); }));
-    TRY(run(c, PSPEC_K_SUMS, 0.0, [&] { launch_catalog_final(part_d, pl.nblk_sum, part_r, pl.nblk_sum, der, c->stream); }));
+    TRY(run(c, PSPEC_K_SUMS, 0.0, [&] {
+      launch_catalog_final(part_d, pl.nblk_sum, part_r, pl.nblk_sum, der, c->stream, der + D_FIX);
+    }));
     bytes += cat_bytes(d) + cat_bytes(r);
   }
   // algorithmic bytes of painting: the particles once and each mesh written once
@@ -490,31 +515,29 @@ pspec_status do_paint(Ctx* c, const pspec_catalog* d, const pspec_catalog* r) {
   const double nmesh = c->p.interlaced ? 2.0 : 1.0;
   const int64_t total = d->count + r->count;
   if (sizeof(T) == 4 && c->tune.paint_binned && pl.max_particles > 0 && total <= pl.max_particles) {
-    TileArgs ta;
-    ta.cnt = c->at<unsigned>(pl.o_tcnt);
-    ta.off = c->at<unsigned>(pl.o_toff);
-    ta.cursor = c->at<unsigned>(pl.o_tcur);
-    ta.rec = c->at<uint4>(pl.o_prec);
-    ta.tile_of = c->at<unsigned>(pl.o_ptile);
-    ta.sorted = c->at<uint4>(pl.o_psort);
+    // exact tile-binned paint: every cell of both meshes is stored, nothing to clear
+    TileArgs ta = tile_args(c);
     e = cudaMemsetAsync(ta.cnt, 0, (size_t)pl.ntiles * sizeof(unsigned), c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "tile counts clear");
     float* f1 = reinterpret_cast<float*>(m1);
     float* f2 = reinterpret_cast<float*>(m2);
     TRY(run(c, PSPEC_K_PAINT, cat_bytes(d), [&] {
-      launch_ptile_prep(ad, c->p.window, 0, der, ta, 0, N, nb, c->stream);
+      launch_ptile_prep(ad, c->p.window, c->p.interlaced, 0, der, ta, 0, N, nb, c->stream);
     }));
     TRY(run(c, PSPEC_K_PAINT, cat_bytes(r), [&] {
-      launch_ptile_prep(ar, c->p.window, 1, der, ta, d->count, N, nb, c->stream);
+      launch_ptile_prep(ar, c->p.window, c->p.interlaced, 1, der, ta, d->count, N, nb, c->stream);
     }));
     TRY(run(c, PSPEC_K_PAINT, 0.0, [&] { launch_ptile_scan(ta, pl.ntiles, c->stream); }));
-    TRY(run(c, PSPEC_K_PAINT, 0.0, [&] { launch_ptile_scatter(ta, total, nullptr, nullptr, nb, c->stream); }));
+    TRY(run(c, PSPEC_K_PAINT, 0.0, [&] { launch_ptile_scatter(ta, total, nullptr, nullptr, N, nb, c->stream); }));
     TRY(run(c, PSPEC_K_PAINT, nmesh * pl.Sr, [&] {
-      launch_ptile_paint(ta, c->p.window, c->p.interlaced, f1, f2, N, c->stream);
+      launch_ptile_paint(ta, c->p.window, c->p.interlaced, f1, f2, N, der + D_FIX, c->stream);
     }));
     c->bytes_paint = bytes + cat_bytes(d) + cat_bytes(r) + nmesh * pl.Sr;
     return PSPEC_OK;
   }
+  e = cudaMemsetAsync(m1, 0, pl.Sr, c->stream);
+  if (e == cudaSuccess && m2) e = cudaMemsetAsync(m2, 0, pl.Sr, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "mesh clear");
   const double frac_d = (double)d->count / (double)(d->count + r->count);
   if (d->count > 0)
     TRY(run(c, PSPEC_K_PAINT, cat_bytes(d) + frac_d * nmesh * pl.Sr, [&] {
@@ -652,8 +675,12 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
         const int Ms = std::min(ms_max, M - hs);
         int rows = std::max(1, pow2_floor(std::max(1, cap / (Ms * tz))));
         while (rows > 1 && (((int64_t)N * N) % rows || PT->smem_ylm(Ms, rows) > kSmemBudget)) rows >>= 1;
-        TRY(run(c, PSPEC_K_YLM_Z, acc(Sr + Ms * Sc), [&] {
-          PT->ylm_z(f, G + hs * stride, stride, ell, h0 + hs, Ms, twh, twr, axis, rows, pl.xp, s);
+        // even l of the SH route read their weights from the Y_lm(rhat) table when the plan holds it
+        const float* rt = pl.has_rtab && ell > 0 && !(ell & 1)
+                              ? c->at<float>(pl.o_rtab) + (int64_t)(ytab_base(ell) + h0 + hs) * N * N * N
+                              : nullptr;
+        TRY(run(c, PSPEC_K_YLM_Z, acc(Sr + Ms * Sc + (rt ? Ms * (double)N * N * N * sizeof(float) : 0.0)), [&] {
+          PT->ylm_z(f, G + hs * stride, stride, ell, h0 + hs, Ms, twh, twr, axis, rows, rt, pl.xp, s);
         }));
       }
       TRY(run(c, PSPEC_K_FFT_Y, acc(M * Sc * (c->frac_yr + c->frac_yw)),
@@ -689,43 +716,35 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
   return PSPEC_OK;
 }
 
-TileArgs tile_args(Ctx* c) {
-  const Plan& pl = c->pl;
-  TileArgs ta;
-  ta.cnt = c->at<unsigned>(pl.o_tcnt);
-  ta.off = c->at<unsigned>(pl.o_toff);
-  ta.cursor = c->at<unsigned>(pl.o_tcur);
-  ta.rec = c->at<uint4>(pl.o_prec);
-  ta.tile_of = c->at<unsigned>(pl.o_ptile);
-  ta.sorted = c->at<uint4>(pl.o_psort);
-  return ta;
-}
-
 // Paint `a` (a data catalog, or randoms with is_randoms = 2) into m1/m2 (zeroed here):
 // tile-binned when `binned`, else direct atomics. `max_count` bounds the particles.
 template <typename T>
-pspec_status paint_one(Ctx* c, const PaintArgs& a, int is_randoms, bool binned, int64_t max_count, T* m1, T* m2) {
+pspec_status paint_one(Ctx* c, const PaintArgs& a, int is_randoms, bool binned, int64_t max_count, T* m1, T* m2,
+                       const double* fix) {
   const Plan& pl = c->pl;
   const int N = pl.g.N;
   const int nb = 16 * c->nsm;
   double* der = c->at<double>(pl.o_derived);
-  cudaError_t e = cudaMemsetAsync(m1, 0, pl.Sr, c->stream);
-  if (e == cudaSuccess && m2) e = cudaMemsetAsync(m2, 0, pl.Sr, c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "mesh clear");
+  cudaError_t e = cudaSuccess;
   const double nmesh = c->p.interlaced ? 2.0 : 1.0;
   const double pbytes = (a.pos_f32 ? 12.0 : 24.0) * (double)max_count;
   if (binned && sizeof(T) == 4) {
     TileArgs ta = tile_args(c);
     e = cudaMemsetAsync(ta.cnt, 0, (size_t)pl.ntiles * sizeof(unsigned), c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "tile counts clear");
-    TRY(run(c, PSPEC_K_PAINT, pbytes, [&] { launch_ptile_prep(a, c->p.window, is_randoms, der, ta, 0, N, nb, c->stream); }));
+    TRY(run(c, PSPEC_K_PAINT, pbytes, [&] {
+      launch_ptile_prep(a, c->p.window, c->p.interlaced, is_randoms, der, ta, 0, N, nb, c->stream);
+    }));
     TRY(run(c, PSPEC_K_PAINT, 0.0, [&] { launch_ptile_scan(ta, pl.ntiles, c->stream); }));
-    TRY(run(c, PSPEC_K_PAINT, 0.0, [&] { launch_ptile_scatter(ta, a.count, a.dc, a.cur, nb, c->stream); }));
+    TRY(run(c, PSPEC_K_PAINT, 0.0, [&] { launch_ptile_scatter(ta, a.count, a.dc, a.cur, N, nb, c->stream); }));
     TRY(run(c, PSPEC_K_PAINT, nmesh * pl.Sr, [&] {
       launch_ptile_paint(ta, c->p.window, c->p.interlaced, reinterpret_cast<float*>(m1), reinterpret_cast<float*>(m2),
-                         N, c->stream);
+                         N, fix, c->stream);
     }));
   } else {
+    e = cudaMemsetAsync(m1, 0, pl.Sr, c->stream);
+    if (e == cudaSuccess && m2) e = cudaMemsetAsync(m2, 0, pl.Sr, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "mesh clear");
     TRY(run(c, PSPEC_K_PAINT, pbytes + nmesh * pl.Sr, [&] {
       launch_paint<T>(a, c->p.window, c->p.interlaced, is_randoms, der, m1, m2, N, nb, c->stream);
     }));
@@ -743,7 +762,7 @@ pspec_status do_set_randoms(Ctx* c, const pspec_catalog* r) {
   T* r1 = c->at<T>(pl.o_rmesh1);
   T* r2 = c->p.interlaced ? c->at<T>(pl.o_rmesh2) : nullptr;
   const bool binned = c->tune.paint_binned && pl.max_particles >= r->count;
-  TRY(paint_one<T>(c, ar, 2, binned, r->count, r1, r2));
+  TRY(paint_one<T>(c, ar, 2, binned, r->count, r1, r2, c->at<double>(pl.o_rsums) + 3));
   return PSPEC_OK;
 }
 
@@ -763,7 +782,7 @@ pspec_status enqueue_mock(Ctx* c, bool binned, int64_t max_count, const int32_t*
   }));
   T* m1 = c->at<T>(pl.o_mesh1);
   T* m2 = c->p.interlaced ? c->at<T>(pl.o_mesh2) : nullptr;
-  TRY(paint_one<T>(c, a, 0, binned, max_count, m1, m2));
+  TRY(paint_one<T>(c, a, 0, binned, max_count, m1, m2, der + D_FIX));
   const int64_t n = (int64_t)pl.g.N * pl.g.N * pl.g.N;
   TRY(run(c, PSPEC_K_OTHER, 3.0 * pl.Sr, [&] { launch_axpy_randoms(m1, c->at<T>(pl.o_rmesh1), n, der, c->stream); }));
   if (m2)
@@ -1258,6 +1277,7 @@ pspec_status pspec_get_plan_info(void* ctx, pspec_plan_info* info) {
   info->kernel_launches = c->launches;
   info->model_bytes_last = c->bytes_paint + c->bytes_mult;
   info->ylm_table_bytes = c->pl.has_ytab ? (int64_t)c->pl.ytab_bytes : 0;
+  info->ylm_rtable_bytes = c->pl.has_rtab ? (int64_t)c->pl.rtab_bytes : 0;
   info->cartesian_table_bytes = (int64_t)c->pl.ctab_bytes;
   return PSPEC_OK;
 }

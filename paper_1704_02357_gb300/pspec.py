@@ -58,7 +58,7 @@ class PlanInfo(C.Structure):
                 ("group_max", C.c_int32), ("bin_ctas", C.c_int32), ("sh_transforms", C.c_int64),
                 ("transforms_executed", C.c_int64), ("kernel_launches", C.c_int64),
                 ("model_bytes_last", C.c_double), ("ylm_table_bytes", C.c_int64),
-                ("cartesian_table_bytes", C.c_int64)]
+                ("cartesian_table_bytes", C.c_int64), ("ylm_rtable_bytes", C.c_int64)]
 
 
 _lib = None
