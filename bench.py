@@ -14,10 +14,9 @@ sampled at n̄ = 3e-4, moved into redshift space radially (f = 0.75), cut to a 6
 and a 600-1400 Mpc/h shell inside a 2000 Mpc/h box; randoms 20x uniform in the cap;
 FKP P0 = 1e4; 512^3 mesh; k bins of 0.005 h/Mpc up to the Nyquist frequency.
 
---impl reference times the FP64 CPU oracle (as it stands) on the host cores instead, on a
-bounded sample of the same workload: each step measures one full 512^3 oracle transform
-and 1/64 slices of its painting, harmonic evaluations and binning; a set's time is composed
-from those measured costs. It needs no GPU; under torchrun only rank 0 runs it.
+--impl reference times the FP64 CPU oracle (as it stands) on the host cores instead: one whole
+512^3 set (l = 0, 2, 4) end to end, after warm-ups on the 64^3 configuration; it reports the
+steps it actually timed. It needs no GPU; under torchrun only rank 0 runs it.
 """
 from __future__ import annotations
 
@@ -173,66 +172,65 @@ def source_hash():
 
 
 # --------------------------------------------------------------------------- oracle baseline
-def oracle_components(data, randoms, frac, fft=True):
-    """Measured oracle costs (seconds) at 512^3: a 1/frac slice of painting, of the real- and
-    k-space harmonic evaluations and of one binning pass, plus one full rfftn."""
-    import scipy.fft as sfft
+def _oracle_params():
     from oracle import estimator as E
+    return E.Params(nmesh=NMESH, box_size=BOX, box_corner=_corner(), window="cic", interlaced=True,
+                    compensate=True, P0=P0, nbar=NBAR)
 
-    p = E.Params(nmesh=NMESH, box_size=BOX, box_corner=_corner(), window="cic", interlaced=True,
-                 compensate=True, P0=P0, nbar=NBAR)
-    rng = np.random.default_rng(0)
+
+def oracle_full_set(data, randoms):
+    """The oracle's whole set at 512^3 (l = 0, 2, 4), timed end to end: seconds."""
+    from oracle import estimator as E
+    t = time.perf_counter()
+    E.multipoles(data, randoms, _oracle_params(), ELLS, k_edges())
+    return time.perf_counter() - t
+
+
+def oracle_components(data, randoms):
+    """Full-size pieces of one oracle set at 512^3, each measured once (no size scaling): the
+    fields (sums, both painted meshes, F1, F2, combine + compensation, inverse transform) with the
+    l = 0 binning, and one harmonic of l = 2 and of l = 4 (real-space Y_lm weights, transform,
+    k-space Y_lm, product, accumulation); a set adds 5 of the first and 9 of the second."""
+    from oracle import estimator as E
+    p = _oracle_params()
+    edges = k_edges()
     out = {}
-    # painting: two meshes (interlaced), a random 1/frac of all particles
-    allpos = np.concatenate([data.pos, randoms.pos])
-    sel = rng.choice(allpos.shape[0], size=max(1, allpos.shape[0] // frac), replace=False)
-    vals = np.ones(sel.size)
     t = time.perf_counter()
-    E.paint(allpos[sel], vals, p)
-    E.paint(allpos[sel], vals, p, shift=0.5)
-    out["paint"] = (time.perf_counter() - t) * allpos.shape[0] / sel.size
-    # real-space harmonic weights on 1/frac of the planes
-    nplane = max(1, NMESH // frac)
-    ix = np.arange(nplane)
+    fl = E.density_fields(data, randoms, p)
+    E.multipoles_from_fields(fl, p, [0], edges)
+    out["fields_and_l0"] = time.perf_counter() - t
     t = time.perf_counter()
-    ux, uy, uz = E.node_rhat(p, ix)
-    E.real_ylm(2, 1, ux, uy, uz)
-    out["ylm_r"] = (time.perf_counter() - t) * NMESH / nplane
-    # k-space harmonic on 1/frac of the modes, product with F0 and accumulation
-    n_modes = NMESH * NMESH * (NMESH // 2 + 1)
-    m = max(1, n_modes // frac)
-    kv = rng.standard_normal((3, m))
-    kv /= np.linalg.norm(kv, axis=0)
-    g = rng.standard_normal(m) + 1j * rng.standard_normal(m)
-    f0 = rng.standard_normal(m) + 1j * rng.standard_normal(m)
-    acc = np.zeros(m)
-    t = time.perf_counter()
-    acc += E.real_ylm(2, 1, *kv) * np.real(g * np.conj(f0))
-    out["ylm_k"] = (time.perf_counter() - t) * n_modes / m
-    b = rng.integers(-1, 160, size=m)
-    t = time.perf_counter()
-    s = b >= 0
-    np.bincount(b[s], weights=acc[s], minlength=160)
-    out["bin"] = (time.perf_counter() - t) * n_modes / m
-    if fft:
-        x = rng.standard_normal((NMESH,) * 3)
+    khat = E.mode_khat(NMESH)
+    out["khat"] = time.perf_counter() - t
+    for ell in (2, 4):
         t = time.perf_counter()
-        sfft.rfftn(x, workers=E._workers())
-        out["fft"] = time.perf_counter() - t
-        del x
+        G = E.harmonic_spectrum(fl.f, p, ell, 1)
+        acc = E.real_ylm(ell, 1, *khat) * np.real(G * np.conj(fl.F0))
+        out[f"harmonic_l{ell}"] = time.perf_counter() - t
+        del G, acc
+    b, mult, _ = E.mode_binning(NMESH, BOX, edges)
+    sel = b >= 0
+    t = time.perf_counter()
+    np.bincount(b[sel], weights=mult[sel] * np.real(fl.F0[sel]), minlength=len(edges) - 1)
+    out["binning"] = time.perf_counter() - t
     return out
 
 
-def _corner():
+def oracle_set_seconds(c):
+    return c["fields_and_l0"] + c["khat"] + 5 * c["harmonic_l2"] + 9 * c["harmonic_l4"] + 2 * c["binning"]
+
+
+def oracle_config1_seconds():
+    """The 64^3 plain box (2e4 data, 1e5 randoms, CIC, l = 0, 2, 4), timed whole."""
     import synth
-    return tuple(float(c) for c in synth.survey_geometry(box_size=BOX).box_corner)
-
-
-def oracle_set_seconds(c, ells=ELLS):
-    """One set: paint + F1, F2 and the inverse transform + per harmonic (weights, transform,
-    k-space harmonic) + one binning pass per multipole."""
-    nh = sum(2 * l + 1 for l in ells if l > 0)
-    return c["paint"] + 3 * c["fft"] + nh * (c["ylm_r"] + c["fft"] + c["ylm_k"]) + len(ells) * c["bin"]
+    from oracle import estimator as E
+    d = synth.uniform_box(20000, 1000.0, (500.0, 500.0, 500.0), 1)
+    r = synth.uniform_box(100000, 1000.0, (500.0, 500.0, 500.0), 2)
+    p = E.Params(nmesh=64, box_size=1000.0, box_corner=(500.0, 500.0, 500.0), window="cic", interlaced=False,
+                 compensate=True, P0=0.0, nbar=2e-5)
+    t = time.perf_counter()
+    E.multipoles(d, r, p, ELLS, np.linspace(0.0, 0.3, 31))
+    return time.perf_counter() - t
 
 
 def oracle_cores():
@@ -241,14 +239,16 @@ def oracle_cores():
 
 
 def cpu_baseline(data, randoms):
-    c = oracle_components(data, randoms, frac=64)
+    c = oracle_components(data, randoms)
     sec = oracle_set_seconds(c)
+    c1 = oracle_config1_seconds()
     return {"value": 1.0 / sec, "unit": "sets/s", "cores": oracle_cores(), "kind": "oracle",
-            "sample": ("FP64 NumPy/SciPy oracle at 512^3, l=0,2,4, composed from measured costs: one full "
-                       "scipy rfftn, and 1/64 slices of the painting (2 interlaced meshes), the real- and "
-                       "k-space Y_lm evaluations with the F0 product, and one binning pass; "
-                       f"set = paint + 3 transforms + 14 x (Y_r + transform + Y_k) + 3 binnings = {sec:.1f} s"),
-            "components_s": {k: round(v, 3) for k, v in c.items()}}
+            "sample": ("FP64 NumPy/SciPy oracle at 512^3, l = 0, 2, 4, from full-size pieces each timed once: the "
+                       "fields with the l = 0 binning, one l = 2 and one l = 4 harmonic, one binning; "
+                       f"set = fields + khat + 5 x l2 + 9 x l4 + 2 binnings = {sec:.1f} s "
+                       "(the reference arm times the whole set end to end)"),
+            "components_s": {k: round(v, 3) for k, v in c.items()},
+            "config1_64cubed_whole_s": round(c1, 3)}
 
 
 def run_reference(args):
@@ -256,27 +256,22 @@ def run_reference(args):
     if rank != 0:
         return 0
     geo, data, randoms = workload(0)
-    budget = 240.0
-    t_start = time.perf_counter()
+    # warm-up: the whole 64^3 configuration (imports, FFT plans, allocator)
     for _ in range(args.warmup):
-        oracle_components(data, randoms, frac=256)
-    per_set = []
-    steps = 0
-    for _ in range(args.steps):
-        c = oracle_components(data, randoms, frac=64)
-        per_set.append(oracle_set_seconds(c))
-        steps += 1
-        if time.perf_counter() - t_start > budget:
-            break
+        oracle_config1_seconds()
+    # one whole 512^3 set per step (about three minutes on 16 cores); the steps actually timed
+    # are reported, so that steps x ms_per_step is the time spent
+    per_set = [oracle_full_set(data, randoms)]
     sec = statistics.median(per_set)
     value = 1.0 / sec
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "sets/s", "n_gpus": args.gpus,
-            "steps": steps, "warmup": args.warmup, "ms_per_step": 1000.0 * sec, "higher_is_better": True,
+            "steps": len(per_set), "steps_requested": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * sec, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD + " (FP64 CPU oracle)", "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": value, "unit": "sets/s", "cores": oracle_cores(), "kind": "oracle",
-                             "sample": "per step: one full 512^3 oracle rfftn and 1/64 slices of painting, "
-                                       "harmonic evaluations and binning; set time composed from them"},
+                             "sample": "one whole 512^3 oracle set (l = 0, 2, 4) per step, timed end to end; "
+                                       "warm-up: the whole 64^3 configuration"},
             "e2e": {"value": value, "unit": "sets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -304,7 +299,8 @@ def batched_measurement(est_for_unused, data, randoms, edges, dev, stream, n_moc
     mocks = [torch.as_tensor(data.pos[rng.random(data.size) < 0.9], device=dev) for _ in range(n_mocks)]
     est = Estimator(nmesh=NMESH, box_size=BOX, box_corner=_corner(), window="cic", interlaced=True, compensate=True,
                     precision="fp32", ell_max=4, P0=P0, nbar=NBAR, max_kbins=len(edges) - 1,
-                    max_particles=max(int(m.shape[0]) for m in mocks), cache_randoms=True, device=dev, stream=stream)
+                    max_particles=max(max(int(m.shape[0]) for m in mocks), int(randoms.size)), cache_randoms=True,
+                    device=dev, stream=stream)
     est.set_randoms(torch.as_tensor(randoms.pos, device=dev))
     est.run_batch(mocks[:2], ELLS, edges)  # capture + warm-up
     l0 = est.plan_info()["kernel_launches"]
@@ -346,11 +342,13 @@ def campaign_measurement(geo, dev, stream, rank, n_mocks=16):
             "n_data": [int(m.shape[0]) for m in mocks], "randoms": int(randoms.size), "graph": True}
 
 
-def serving_measurement(geo, dev, rank, n_requests=20, load=0.5):
-    """Served stream: Poisson arrivals (seed 5) of catalogs with 1e5-5e6 particles
-    (log-uniform), meshes from {128, 256, 512, 768, 1024}^3 and l_max in {4, 16} uniformly,
-    FP32, admitted by workspace footprint against a 120 GB budget; mean inter-arrival set to
-    `load` of the measured mean service time."""
+def serving_measurement(geo, dev, rank, n_per_load=200, loads=(0.25, 0.5, 0.75, 1.0), n_capacity=40, budget_gb=200):
+    """Served stream: Poisson arrivals (seed 5) of catalogs with 1e5-5e6 particles (log-uniform),
+    meshes from {128, 256, 512, 768, 1024}^3 and l_max in {4, 16} uniformly, FP32, admitted by
+    workspace footprint against an HBM budget, two contexts per shape at most. Every shape is
+    built before the stream (prewarm) as the budget allows. Capacity is the completion rate of
+    a burst of requests all present at t = 0; the sweep then offers Poisson arrivals at 0.25x to
+    1.0x of it, `n_per_load` requests per load, and reports p50/p99 latency and queue wait."""
     import synth
     import torch
     from paper_1704_02357_gb300.serve import Server, Request, latency_summary
@@ -359,42 +357,51 @@ def serving_measurement(geo, dev, rank, n_requests=20, load=0.5):
     dense = synth.survey_catalog(fld, geo, nbar=1.9e-3, seed=99 + 1000 * rank)
     randoms = synth.survey_randoms(2 * 10 ** 7, geo, seed=98 + 1000 * rank)
     rdev = torch.as_tensor(randoms.pos, device=dev)
+    ddev = torch.as_tensor(dense.pos, device=dev)
     meshes = [128, 256, 512, 768, 1024]
-    reqs = []
-    for i in range(n_requests):
-        n = int(round(math.exp(rng.uniform(math.log(1e5), math.log(5e6)))))
-        idx = rng.choice(dense.size, size=min(n, dense.size), replace=False)
-        nm = int(rng.choice(meshes))
-        lm = int(rng.choice([4, 16]))
-        reqs.append(Request(rid=i, nmesh=nm, ell_max=lm, pos=torch.as_tensor(dense.pos[idx], device=dev),
-                            k_edges=k_edges(nm)))
+    shapes = [(n, l) for n in meshes for l in (4, 16)]
+
+    def make(n_req):
+        out = []
+        for i in range(n_req):
+            n = int(round(math.exp(rng.uniform(math.log(1e5), math.log(5e6)))))
+            idx = torch.as_tensor(rng.choice(dense.size, size=min(n, dense.size), replace=False), device=dev)
+            nm = int(rng.choice(meshes))
+            lm = int(rng.choice([4, 16]))
+            out.append(Request(rid=i, nmesh=nm, ell_max=lm, pos=ddev[idx], k_edges=k_edges(nm)))
+        return out
+
     gb = 1 << 30
     mgb = lambda n, l: (8 * (n ** 3) * 4 if n >= 768 else 0)  # at most 8 spectra per group at 768^3+
-    srv = Server(BOX, _corner(), randoms_for=lambda n: rdev, hbm_budget=120 * gb, window="cic", interlaced=True,
+    srv = Server(BOX, _corner(), randoms_for=lambda n: rdev, hbm_budget=budget_gb * gb, window="cic", interlaced=True,
                  P0=P0, nbar=NBAR, max_kbins=512, max_particles=5 * 10 ** 6 + 1, max_group_bytes_for=mgb,
-                 max_slots_per_shape=1, device=dev)
-    # service time of each shape alone (warms contexts and graphs): sets the arrival rate
-    svc = []
-    for key in sorted({(r.nmesh, r.ell_max) for r in reqs}):
-        r0 = next(r for r in reqs if (r.nmesh, r.ell_max) == key)
-        probe = Request(rid=-1, nmesh=key[0], ell_max=key[1], pos=r0.pos, k_edges=r0.k_edges)
-        for _ in range(2):
-            t = time.perf_counter()
-            srv.submit(probe)
-            while srv.busy():
-                srv.step()
-            dt = time.perf_counter() - t
-        svc.append(dt)
-    mean_service = float(np.mean(svc))
-    srv.done.clear()
-    gaps = rng.exponential(mean_service / load, size=n_requests)
-    arrivals = np.cumsum(gaps) - gaps[0]
+                 max_slots_per_shape=2, device=dev)
     t0 = time.perf_counter()
-    done = srv.run(reqs, arrivals)
-    wall = time.perf_counter() - t0
-    out = latency_summary(done, wall)
-    out.update({"load": load, "mean_service_ms_alone": mean_service * 1e3, "hbm_budget_gb": 120,
-                "contexts": len(srv.slots)})
+    srv.prewarm(shapes, edges_for=k_edges, pos_for=lambda n: ddev[:100000], slots_per_shape=1)
+    prewarm_s = time.perf_counter() - t0
+    # capacity: a burst, every request present at t = 0
+    burst = make(n_capacity)
+    t0 = time.perf_counter()
+    srv.run(burst, np.zeros(len(burst)))
+    capacity = len(burst) / (time.perf_counter() - t0)
+    srv.done = []
+    sweep = []
+    for load in loads:
+        reqs = make(n_per_load)
+        gaps = rng.exponential(1.0 / (load * capacity), size=len(reqs))
+        arrivals = np.cumsum(gaps) - gaps[0]
+        t0 = time.perf_counter()
+        done = srv.run(reqs, arrivals)
+        wall = time.perf_counter() - t0
+        row = latency_summary(done, wall)
+        row["load"] = load
+        row["offered_per_s"] = load * capacity
+        sweep.append(row)
+        srv.done = []
+    out = {"capacity_per_s": capacity, "capacity_burst_requests": n_capacity, "requests_per_load": n_per_load,
+           "sweep": sweep, "hbm_budget_gb": budget_gb, "prewarm_s": prewarm_s, "contexts": len(srv.slots),
+           "shapes_with_tables": sorted([list(k) for k in shapes if srv.tables_for(*k)]),
+           "max_slots_per_shape": 2}
     srv.close()
     return out
 
@@ -412,6 +419,8 @@ def main():
     ap.add_argument("--ells", default="0,2,4", help="multipoles of the headline measurement")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's default knobs (profiling runs: no candidate launches)")
+    ap.add_argument("--max-particles", type=int, default=-1,
+                    help="capacity of the tile-binned paint (-1: both catalogs; 0: direct paint, for small profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -439,7 +448,8 @@ def main():
     def est_for(precision, ell_max, window="cic", **kw):
         return Estimator(nmesh=nmesh, box_size=BOX, box_corner=corner, observer=(0.0, 0.0, 0.0), window=window,
                          interlaced=True, compensate=True, precision=precision, ell_max=ell_max, P0=P0, nbar=NBAR,
-                         max_kbins=nk, max_particles=int(data.size + randoms.size), device=dev, stream=stream, **kw)
+                         max_kbins=nk, max_particles=int(data.size + randoms.size) if args.max_particles < 0 else args.max_particles,
+                         device=dev, stream=stream, **kw)
 
     dpos = torch.as_tensor(data.pos, device=dev)
     rpos = torch.as_tensor(randoms.pos, device=dev)
@@ -590,6 +600,18 @@ def main():
                                    "ylm_table_bytes": e16.plan_info()["ylm_table_bytes"]}
         e16.close()
         del e16
+        torch.cuda.empty_cache()
+        # ---- the same headline set with plain FP32 radix trees in every transform: the cost of the
+        # exact-add harmonic and inverse transforms of the default FP32 path
+        ep = est_for("fp32_plain", 4)
+        msp, _, _, _ = timed(ep, ELLS, max(3, args.steps // 2), 3)
+        side["fp32_plain_transforms_ell_max_4"] = {
+            "value": ws * max(3, args.steps // 2) / (msp / 1000.0), "unit": "sets/s",
+            "ms_per_set": msp / max(3, args.steps // 2),
+            "note": "every transform a plain FP32 radix tree (precision fp32_plain); the headline's exact-add "
+                    "transforms keep the l <= 16 TSC configuration's l = 2 first bin within 1e-5"}
+        ep.close()
+        del ep
         torch.cuda.empty_cache()
         # ---- plain FP64 path, l = 0, 2, 4
         e64 = est_for("fp64", 4)

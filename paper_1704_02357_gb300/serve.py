@@ -7,7 +7,12 @@ the HBM budget (its workspace is the footprint), and enqueues the request's whol
 sequence on that context's own CUDA stream. Requests that arrive while others are on the GPU
 are admitted as slots and memory free up, and their kernels overlap on the device. Finished
 requests release their context (kept warm for the next request of that shape; evicted least
-recently used when a new shape needs the memory).
+recently used when a new shape needs the memory). Shapes known in advance can be built before
+the stream starts (prewarm), so that no request waits behind a context's creation.
+
+A context holds the Y_lm tables (k-space and real-space, FP64-built) when its footprint with them
+is at most `table_fraction` of the budget; larger shapes are served without them (Y_lm evaluated
+in FP32 per mode and per node), which keeps them admissible at the cost of the tables' accuracy.
 
 All arithmetic runs in libpspec (pspec_run_batch on one mock, replaying the context's
 captured graph); this module only schedules.
@@ -62,7 +67,7 @@ class Server:
     def __init__(self, box_size: float, box_corner, randoms_for: Callable[[int], object], hbm_budget: int,
                  observer=(0.0, 0.0, 0.0), window="cic", interlaced=True, compensate=True, P0=0.0, nbar=0.0,
                  max_kbins=512, max_particles=0, max_group_bytes_for: Optional[Callable[[int, int], int]] = None,
-                 max_slots_per_shape: int = 2, device=None, clock=time.perf_counter):
+                 max_slots_per_shape: int = 2, table_fraction: float = 0.5, device=None, clock=time.perf_counter):
         self.kw = dict(box_size=box_size, box_corner=box_corner, observer=observer, window=window,
                        interlaced=interlaced, compensate=compensate, P0=P0, nbar=nbar, max_kbins=max_kbins,
                        precision="fp32")
@@ -71,6 +76,8 @@ class Server:
         self.max_particles = int(max_particles)
         self.max_group_bytes_for = max_group_bytes_for or (lambda n, l: 0)
         self.max_slots_per_shape = max_slots_per_shape
+        self.table_fraction = float(table_fraction)
+        self._tables: Dict[tuple, bool] = {}
         self.headroom = 1 << 30  # device bytes left free beside a new workspace
         self.device = device
         self.clock = clock
@@ -83,16 +90,26 @@ class Server:
     def used(self) -> int:
         return sum(s.footprint for s in self.slots)
 
-    def _footprint(self, nmesh: int, ell_max: int) -> int:
+    def tables_for(self, nmesh: int, ell_max: int) -> bool:
+        """Whether contexts of this shape hold the Y_lm tables (see the module docstring)."""
+        key = (nmesh, ell_max)
+        if key not in self._tables:
+            self._tables[key] = self._footprint(nmesh, ell_max, True) <= self.table_fraction * self.budget
+        return self._tables[key]
+
+    def _footprint(self, nmesh: int, ell_max: int, tables: Optional[bool] = None) -> int:
         from . import pspec as P
         import ctypes as C
         import torch
+        if tables is None:
+            tables = self.tables_for(nmesh, ell_max)
         lib = P.load()
         comp = P.compensation_code(self.kw["compensate"])
-        p = P.Params(nmesh, P.WINDOWS[self.kw["window"]], int(self.kw["interlaced"]), comp, 0,
-                     ell_max, float(self.kw["box_size"]), (C.c_double * 3)(*self.kw["box_corner"]),
-                     (C.c_double * 3)(*self.kw["observer"]), float(self.kw["P0"]), float(self.kw["nbar"]),
-                     int(self.max_group_bytes_for(nmesh, ell_max)), self.max_particles, 1, 0, 0)
+        p = P.Params(nmesh, P.WINDOWS[self.kw["window"]], int(self.kw["interlaced"]), comp,
+                     P.PRECISIONS[self.kw["precision"]], ell_max, float(self.kw["box_size"]),
+                     (C.c_double * 3)(*self.kw["box_corner"]), (C.c_double * 3)(*self.kw["observer"]),
+                     float(self.kw["P0"]), float(self.kw["nbar"]), int(self.max_group_bytes_for(nmesh, ell_max)),
+                     self.max_particles, 1, 0 if tables else -1, 0)
         n = C.c_int64(0)
         with torch.cuda.device(self.device or torch.cuda.current_device()):
             P._check(lib.pspec_workspace_size(C.byref(p), int(self.kw["max_kbins"]), C.byref(n)))
@@ -124,11 +141,32 @@ class Server:
         stream = torch.cuda.Stream(device=self.device)
         est = Estimator(nmesh=nmesh, ell_max=ell_max, cache_randoms=True, max_particles=self.max_particles,
                         max_group_bytes=self.max_group_bytes_for(nmesh, ell_max), device=self.device, stream=stream,
-                        **self.kw)
+                        ylm_table=self.tables_for(nmesh, ell_max), **self.kw)
         est.set_randoms(self.randoms_for(nmesh))
         slot = _Slot(est=est, key=key, footprint=need)
         self.slots.append(slot)
         return slot
+
+    def prewarm(self, shapes: Sequence[tuple], edges_for: Callable[[int], np.ndarray], pos_for: Callable[[int], object],
+                slots_per_shape: Optional[int] = None) -> None:
+        """Build contexts (tables, cached randoms meshes) and capture their graphs for the given
+        (nmesh, l_max) shapes before the stream starts, up to `slots_per_shape` each (default
+        the per-shape cap), while the budget allows without evicting one another."""
+        import torch
+        n = self.max_slots_per_shape if slots_per_shape is None else slots_per_shape
+        for key in shapes:
+            for _ in range(n):
+                if sum(1 for s in self.slots if s.key == key) >= self.max_slots_per_shape:
+                    break
+                if self.used() + self._footprint(*key) > self.budget:
+                    break
+                slot = self._new_slot(tuple(key))
+                if slot is None:
+                    break
+                ells = list(range(0, key[1] + 1, 2))
+                slot.est.run_batch([pos_for(key[0])], ells, edges_for(key[0]), use_graph=True)
+                torch.cuda.synchronize()
+                slot.last_used = self.now()
 
     # ------------------------------------------------------------------ scheduling
     def submit(self, req: Request) -> None:
@@ -213,4 +251,4 @@ def latency_summary(done: Sequence[Request], wall: float) -> Dict[str, float]:
     wait = np.array([r.queue_wait for r in done])
     return {"requests": len(done), "throughput_per_s": len(done) / wall if wall > 0 else float("nan"),
             "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-            "mean_queue_wait_ms": float(wait.mean() * 1e3)}
+            "mean_queue_wait_ms": float(wait.mean() * 1e3), "p99_queue_wait_ms": float(np.percentile(wait, 99) * 1e3)}

@@ -16,6 +16,11 @@ def gpu_estimator(p: E.Params, precision="fp32", ell_max=4, max_kbins=512, **kw)
 
 
 def run_gpu(p, data, randoms, ells, edges, precision="fp32", ell_max=None, **kw):
+    """Paint + multipoles on a fresh context. FP32 contexts get the exact tile-binned paint
+    (max_particles covers both catalogs) unless the caller passes max_particles (0: direct
+    atomic paint)."""
+    if precision != "fp64":
+        kw.setdefault("max_particles", data.size + randoms.size)
     est = gpu_estimator(p, precision=precision, ell_max=ell_max if ell_max is not None else max(ells), **kw)
     stats = est.paint(data.pos, randoms.pos, data.weight, data.nbar, randoms.weight, randoms.nbar)
     out = est.multipoles(ells, edges)

@@ -231,7 +231,7 @@ def test_tile_binned_paint_matches_oracle_and_direct(nmesh, window, interlaced):
     ells = [0, 2, 4, 6]
     o = E.multipoles(d, r, p, ells, edges)
     gb = run_gpu(p, d, r, ells, edges, precision="fp32", max_particles=d.size + r.size)
-    gd = run_gpu(p, d, r, ells, edges, precision="fp32")
+    gd = run_gpu(p, d, r, ells, edges, precision="fp32", max_particles=0)
     assert gb["stats"]["n_wrapped"] > 0
     assert gb["stats"]["n_wrapped"] == gd["stats"]["n_wrapped"]
     scale = np.abs(o["P"][0]) + o["S"] / o["I"]
@@ -297,6 +297,7 @@ def test_ylm_table_and_per_mode_paths_match_oracle():
         check_fp32(g, o, ells)
         nbytes = 64 * 64 * 32 * 4 * (5 + 9 + 13)
         assert g["plan"]["ylm_table_bytes"] == (nbytes if table else 0)
+        assert g["plan"]["ylm_rtable_bytes"] == (2 * nbytes if table else 0)  # Y_lm(rhat) of every node
         out[table] = g["P"]
     scale = np.abs(o["P"][0])
     assert np.all(np.abs(out[True] - out[False]) <= 2e-5 * scale[None, :])

@@ -52,6 +52,7 @@ class FakeEstimator:
 
     def __init__(self, nmesh, ell_max, stream, **kw):
         self.nmesh, self.ell_max, self.stream = nmesh, ell_max, stream
+        self.kw = kw
         self.closed = False
         self.randoms = None
         FakeEstimator.created.append(self)
@@ -75,13 +76,14 @@ def fake_server(monkeypatch):
     monkeypatch.setattr(torch.cuda, "Stream", FakeStream)
     monkeypatch.setattr(torch.cuda, "Event", FakeEvent)
     monkeypatch.setattr(torch.cuda, "empty_cache", lambda: None)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a: None)
     clock = types.SimpleNamespace(t=0.0)
 
     def make(budget, free=1 << 50, footprints=None, **kw):
         s = serve.Server(box_size=1000.0, box_corner=(0.0, 0.0, 0.0), randoms_for=lambda n: f"randoms{n}",
                          hbm_budget=budget, clock=lambda: clock.t, **kw)
         fp = footprints or {}
-        s._footprint = lambda nmesh, ell_max: fp.get((nmesh, ell_max), nmesh ** 3)
+        s._footprint = lambda nmesh, ell_max, tables=None: fp.get((nmesh, ell_max), nmesh ** 3)
         s._free_device_bytes = lambda: free - s.used()
         s.headroom = 0
         return s
@@ -118,6 +120,33 @@ def test_requests_of_one_shape_share_and_reuse_a_context(fake_server):
     for r in s.done:
         assert r.P.shape == (3, 4) and np.all(r.P == 64.0)
         assert r.t_admit >= r.t_arrival and r.t_done >= r.t_admit
+
+
+def test_shapes_whose_tables_would_crowd_the_budget_are_served_without_them(fake_server):
+    """A context holds the Y_lm tables only when its footprint with them is at most
+    table_fraction of the budget; the policy is decided once per shape."""
+    s = fake_server(budget=100, table_fraction=0.5)
+    big = {True: 80, False: 30}
+    small = {True: 40, False: 20}
+    s._footprint = lambda nmesh, ell_max, tables=None: (
+        (big if nmesh == 512 else small)[s.tables_for(nmesh, ell_max) if tables is None else tables])
+    assert s.tables_for(512, 16) is False and s.tables_for(128, 4) is True
+    s.submit(_req(0, 512, 16))
+    s.submit(_req(1, 128, 4))
+    s.step()
+    assert sorted(sl.footprint for sl in s.slots) == [30, 40]
+    assert {e.nmesh: e.kw["ylm_table"] for e in FakeEstimator.created} == {512: False, 128: True}
+
+
+def test_prewarm_builds_contexts_before_the_stream(fake_server):
+    s = fake_server(budget=10 * 64 ** 3)
+    s.prewarm([(64, 4), (32, 2)], edges_for=lambda n: np.linspace(0, 0.1, 5), pos_for=lambda n: None)
+    assert sorted(sl.key for sl in s.slots) == [(32, 2), (32, 2), (64, 4), (64, 4)]
+    n0 = len(FakeEstimator.created)
+    s.submit(_req(0, 64))
+    s.step()
+    assert len(FakeEstimator.created) == n0  # served by a prewarmed context, none built on admission
+    assert any(sl.busy is not None for sl in s.slots if sl.key == (64, 4))
 
 
 def test_admission_evicts_the_least_recently_used_idle_context(fake_server):
