@@ -172,6 +172,11 @@ def source_hash():
 
 
 # --------------------------------------------------------------------------- oracle baseline
+def _corner():
+    import synth
+    return tuple(float(c) for c in synth.survey_geometry(box_size=BOX).box_corner)
+
+
 def _oracle_params():
     from oracle import estimator as E
     return E.Params(nmesh=NMESH, box_size=BOX, box_corner=_corner(), window="cic", interlaced=True,
@@ -419,6 +424,10 @@ def main():
     ap.add_argument("--ells", default="0,2,4", help="multipoles of the headline measurement")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's default knobs (profiling runs: no candidate launches)")
+    ap.add_argument("--serving-requests", type=int, default=40,
+                    help="requests per load point of the served-stream sweep (the full sweep: 200)")
+    ap.add_argument("--serving-loads", default="0.25,0.5,1.0",
+                    help="offered loads of the sweep, as fractions of the measured capacity")
     ap.add_argument("--max-particles", type=int, default=-1,
                     help="capacity of the tile-binned paint (-1: both catalogs; 0: direct paint, for small profiling runs)")
     args = ap.parse_args()
@@ -660,7 +669,8 @@ def main():
         torch.cuda.empty_cache()
         side["mock_campaign"] = campaign_measurement(geo, dev, stream, rank)
         torch.cuda.empty_cache()
-        side["serving"] = serving_measurement(geo, dev, rank)
+        side["serving"] = serving_measurement(geo, dev, rank, n_per_load=args.serving_requests,
+                                              loads=tuple(float(x) for x in args.serving_loads.split(",")))
         torch.cuda.empty_cache()
 
     cpu = None
