@@ -269,7 +269,10 @@ class Estimator:
         edges = np.ascontiguousarray(k_edges, dtype=np.float64)
         nk = len(edges) - 1
         if bins is None:
-            bins = torch.empty((1 + len(ells), nk), dtype=torch.float64, device=self.device)
+            # allocated on the context's stream, which writes it (the caching allocator keeps it
+            # there until that stream's work on it is done)
+            with torch.cuda.stream(self.stream):
+                bins = torch.empty((1 + len(ells), nk), dtype=torch.float64, device=self.device)
         el = (C.c_int32 * len(ells))(*ells)
         _check(lib.pspec_multipoles_range(self._ctx, el, len(ells), edges.ctypes.data_as(C.POINTER(C.c_double)), nk,
                                           int(q0), int(q1), int(bool(include_p0)), C.c_void_p(_ptr(bins))), self._ctx)
@@ -282,9 +285,10 @@ class Estimator:
         ells = [int(e) for e in ells]
         edges = np.ascontiguousarray(k_edges, dtype=np.float64)
         nk = len(edges) - 1
-        P = torch.empty((len(ells), nk), dtype=torch.float64, device=self.device)
-        km = torch.empty(nk, dtype=torch.float64, device=self.device)
-        nm = torch.empty(nk, dtype=torch.float64, device=self.device)
+        with torch.cuda.stream(self.stream):  # written by the context's stream
+            P = torch.empty((len(ells), nk), dtype=torch.float64, device=self.device)
+            km = torch.empty(nk, dtype=torch.float64, device=self.device)
+            nm = torch.empty(nk, dtype=torch.float64, device=self.device)
         el = (C.c_int32 * len(ells))(*ells)
         _check(lib.pspec_finalize_bins(self._ctx, C.c_void_p(_ptr(bins)), el, len(ells),
                                        edges.ctypes.data_as(C.POINTER(C.c_double)), nk, C.c_void_p(_ptr(P)),
@@ -315,10 +319,11 @@ class Estimator:
             m = m if isinstance(m, (tuple, list)) else (m,)
             cats.append(_catalog(m[0], m[1] if len(m) > 1 else None, m[2] if len(m) > 2 else None, self.device, keep))
         arr = (Catalog * len(cats))(*cats)
-        P = torch.empty((len(cats), len(ells), nk), dtype=torch.float64, device=self.device)
-        sums = torch.empty((len(cats), 4), dtype=torch.float64, device=self.device)
-        km = torch.empty(nk, dtype=torch.float64, device=self.device)
-        nm = torch.empty(nk, dtype=torch.float64, device=self.device)
+        with torch.cuda.stream(self.stream):  # written by the context's stream
+            P = torch.empty((len(cats), len(ells), nk), dtype=torch.float64, device=self.device)
+            sums = torch.empty((len(cats), 4), dtype=torch.float64, device=self.device)
+            km = torch.empty(nk, dtype=torch.float64, device=self.device)
+            nm = torch.empty(nk, dtype=torch.float64, device=self.device)
         el = (C.c_int32 * len(ells))(*ells)
         _check(load().pspec_run_batch(self._ctx, arr, len(cats), el, len(ells),
                                       edges.ctypes.data_as(C.POINTER(C.c_double)), nk, C.c_void_p(P.data_ptr()),
@@ -396,8 +401,9 @@ def wedges(P, ells: Sequence[int], mu_edges, stream=None):
     mu = np.ascontiguousarray(mu_edges, dtype=np.float64)
     ells = [int(e) for e in ells]
     n_mu = len(mu) - 1
-    out = torch.empty((n_mu, P.shape[1]), dtype=torch.float64, device=P.device)
     s = stream if stream is not None else torch.cuda.current_stream(P.device)
+    with torch.cuda.stream(s):  # written by the kernel on `s`
+        out = torch.empty((n_mu, P.shape[1]), dtype=torch.float64, device=P.device)
     el = (C.c_int32 * len(ells))(*ells)
     _check(lib.pspec_wedges(C.c_void_p(P.data_ptr()), el, len(ells), int(P.shape[1]),
                             mu.ctypes.data_as(C.POINTER(C.c_double)), n_mu, C.c_void_p(out.data_ptr()),

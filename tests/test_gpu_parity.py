@@ -171,6 +171,30 @@ def test_wedges_match_oracle():
     np.testing.assert_allclose(out.cpu().numpy(), E.wedges(P, ells, mu), rtol=1e-13, atol=1e-14)
 
 
+def test_wedges_of_host_multipoles_through_a_device_copy():
+    """The boundary as a caller uses it: pspec_multipoles returns host P_l; the caller copies
+    them to the device and pspec_wedges combines them there (Sec. 2.2 eqs. wedge-est, Lbar).
+    Against the oracle's wedges of the oracle's multipoles, and exactly the oracle's wedges of
+    the host P (the wedge step is FP64 on both sides)."""
+    import torch
+    from paper_1704_02357_gb300 import wedges
+    d, r, p, edges = _offnode(48, "tsc", True, seed=31)
+    ells = [0, 2, 4, 6]
+    mu = np.array([0.0, 0.05, 0.2, 0.4, 0.6, 0.8, 1.0])
+    g = run_gpu(p, d, r, ells, edges, precision="fp32")          # host arrays out
+    Pd = torch.as_tensor(g["P"]).to("cuda")                      # the caller's device copy
+    out = wedges(Pd, ells, mu)
+    torch.cuda.synchronize()
+    w = out.cpu().numpy()
+    np.testing.assert_allclose(w, E.wedges(g["P"], ells, mu), rtol=1e-13, atol=1e-12 * np.abs(g["P"]).max())
+    o = E.multipoles(d, r, p, ells, edges)
+    wo = E.wedges(o["P"], ells, mu)
+    scale = np.abs(o["P"][0]) + o["S"] / o["I"]
+    # |Lbar_l| <= 1, so a wedge moves by at most the sum of the multipoles' tolerances
+    bound = sum(1e-5 if ell <= 4 else 1e-4 for ell in ells) * scale
+    assert np.all(np.abs(w - wo) <= bound[None, :])
+
+
 def test_errors_are_reported_not_faulted():
     from paper_1704_02357_gb300 import PspecError
     from paper_1704_02357_gb300 import pspec

@@ -168,3 +168,77 @@ def test_dropping_a_rank_share_is_detected():
     P_full = sh.finalize_bins(full, ELLS, edges)["P"]
     P_part = sh.finalize_bins(part, ELLS, edges)["P"]
     assert np.max(np.abs(P_full[2] - P_part[2])) > 1e-6 * np.max(np.abs(P_full[0]))
+
+
+class ContractShard(OracleShard):
+    """OracleShard that checks every call against the contract of Estimator.multipoles_range /
+    finalize_bins (pspec_multipoles_range, pspec_finalize_bins): the range [q0, q1) is this
+    rank's contiguous share of the flat harmonic list, only rank 0 asks for the l = 0 bins, the
+    raw bins are a float64 torch tensor of shape (1 + n_ells, nk) whose row 0 is zero without
+    include_p0, and finalize_bins receives that same tensor, summed over the ranks in place."""
+
+    def __init__(self, params, data, randoms, rank, world):
+        super().__init__(params, data, randoms)
+        self.rank, self.world = rank, world
+        self.calls = []
+
+    def multipoles_range(self, ells, k_edges, q0, q1, include_p0=True):
+        assert (q0, q1) == split(len(harmonic_items(ells)), self.world, self.rank)
+        assert bool(include_p0) == (self.rank == 0)
+        bins = super().multipoles_range(ells, k_edges, q0, q1, include_p0=include_p0)
+        assert bins.dtype == self.torch.float64 and tuple(bins.shape) == (1 + len(ells), len(k_edges) - 1)
+        if not include_p0:
+            assert not bins[0].any()
+        self.local = bins.clone()
+        self.bins = bins
+        self.calls.append(("range", q0, q1, bool(include_p0)))
+        return bins
+
+    def finalize_bins(self, bins, ells, k_edges):
+        assert bins is self.bins  # the all-reduce works in place on the returned tensor
+        self.calls.append(("finalize",))
+        return super().finalize_bins(bins, ells, k_edges)
+
+
+def _contract_rank(rank, world, port, out_dir):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        p, data, randoms, edges = _case()
+        sh = ContractShard(p, data, randoms, rank, world)
+        res = sharded_multipoles(sh, ELLS, edges)
+        assert [c[0] for c in sh.calls] == ["range", "finalize"]
+        np.save(os.path.join(out_dir, f"P{rank}.npy"), res["P"])
+        np.save(os.path.join(out_dir, f"local{rank}.npy"), sh.local.numpy())
+        np.save(os.path.join(out_dir, f"summed{rank}.npy"), sh.bins.numpy())
+    finally:
+        dist.destroy_process_group()
+
+
+def test_sharded_multipoles_follow_the_range_contract_over_gloo():
+    """Two gloo ranks drive sharded_multipoles through a stand-in that checks the product's
+    range contract; the summed bins are the sum of the ranks' local bins, the same on both
+    ranks, and finalize to the oracle's single-process multipoles."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    world = 2
+    with tempfile.TemporaryDirectory() as d:
+        port = _free_port()
+        procs = [ctx.Process(target=_contract_rank, args=(r, world, port, d)) for r in range(world)]
+        for pr in procs:
+            pr.start()
+        for pr in procs:
+            pr.join(timeout=240)
+        assert all(pr.exitcode == 0 for pr in procs), [pr.exitcode for pr in procs]
+        local = [np.load(os.path.join(d, f"local{r}.npy")) for r in range(world)]
+        summed = [np.load(os.path.join(d, f"summed{r}.npy")) for r in range(world)]
+        Ps = [np.load(os.path.join(d, f"P{r}.npy")) for r in range(world)]
+    np.testing.assert_array_equal(summed[0], summed[1])
+    np.testing.assert_allclose(summed[0], local[0] + local[1], rtol=1e-15, atol=0)
+    assert local[0][0].any() and not local[1][0].any()
+    p, data, randoms, edges = _case()
+    o = E.multipoles(data, randoms, p, ELLS, edges)
+    scale = (np.abs(o["P"][0]) + o["S"] / o["I"]).max()
+    np.testing.assert_allclose(Ps[0], o["P"], rtol=1e-10, atol=1e-12 * scale)
