@@ -56,6 +56,7 @@ struct Plan {
   bool has_ytab = false, has_ctab = false, has_rtab = false;
   size_t ytab_bytes = 0, o_ytab = 0, ctab_bytes = 0, o_ctab = 0, rtab_bytes = 0, o_rtab = 0;
   size_t o_xtiles;  // x-pass tiles (j, kz-tile) of the binning pass that hold a binned mode, in order
+  size_t o_twh12 = 0, o_twf12 = 0, o_twr12 = 0;  // twiddles of the exact-add stages (FP32)
   size_t o_mesh1, o_mesh2, o_f0, o_w, o_f, o_g, o_twh, o_twf, o_twr, o_axis, o_phase, o_invw, o_bin, o_kmag, o_cnt,
       o_lo, o_hi, o_nmodes, o_ksum, o_sums, o_derived, o_bins, o_out, o_tcnt, o_toff, o_tcur, o_prec, o_ptile,
       o_psort, total;
@@ -152,6 +153,11 @@ pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl,
   pl->o_twh = take(NH * usz);
   pl->o_twf = take(N * usz);
   pl->o_twr = take(NH * usz);
+  if (pl->xp) {
+    pl->o_twh12 = take(NH * sizeof(float4));
+    pl->o_twf12 = take(N * sizeof(float4));
+    pl->o_twr12 = take(NH * sizeof(float4));
+  }
   pl->o_axis = take(3 * (size_t)N * pl->esz);
   pl->o_phase = take(3 * (size_t)N * usz);
   pl->o_invw = take((N + NH) * csz);
@@ -297,6 +303,12 @@ template <> ux<float> unit_factor<float>(double a) {
   return make_float4(ch, sh, (float)(c - (double)ch), (float)(s - (double)sh));
 }
 template <> ux<double> unit_factor<double>(double a) { return make_double2(std::cos(a), std::sin(a)); }
+// The form the exact-add stages use: {c12, s12, c - c12, s - s12}, c12 and s12 multiples of 2^-12.
+float4 unit_factor12(double a) {
+  const double c = std::cos(a), s = std::sin(a);
+  const double c12 = std::nearbyint(c * 4096.0) / 4096.0, s12 = std::nearbyint(s * 4096.0) / 4096.0;
+  return make_float4((float)c12, (float)s12, (float)(c - c12), (float)(s - s12));
+}
 
 template <typename T>
 pspec_status upload_tables(Ctx* c) {
@@ -340,6 +352,17 @@ pspec_status upload_tables(Ctx* c) {
   e = cudaMemcpyAsync(c->at<U>(pl.o_twh), twh.data(), NH * sizeof(U), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->at<U>(pl.o_twf), twf.data(), N * sizeof(U), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->at<U>(pl.o_twr), twr.data(), NH * sizeof(U), cudaMemcpyHostToDevice, c->stream);
+  std::vector<float4> twh12(NH), twf12(N), twr12(NH);
+  if (pl.xp) {
+    for (int t = 0; t < NH; t++) {
+      twh12[t] = unit_factor12(-2.0 * M_PI * t / NH);
+      twr12[t] = unit_factor12(-2.0 * M_PI * t / N);
+    }
+    for (int t = 0; t < N; t++) twf12[t] = unit_factor12(-2.0 * M_PI * t / N);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->at<float4>(pl.o_twh12), twh12.data(), NH * sizeof(float4), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->at<float4>(pl.o_twf12), twf12.data(), N * sizeof(float4), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->at<float4>(pl.o_twr12), twr12.data(), NH * sizeof(float4), cudaMemcpyHostToDevice, c->stream);
+  }
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->at<T>(pl.o_axis), axis.data(), 3 * N * sizeof(T), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->at<U>(pl.o_phase), phase.data(), 3 * N * sizeof(U), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->at<C>(pl.o_invw), invw.data(), (N + NH) * sizeof(C), cudaMemcpyHostToDevice, c->stream);
@@ -578,6 +601,10 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
   const U* twh = c->at<U>(pl.o_twh);
   const U* twf = c->at<U>(pl.o_twf);
   const U* twr = c->at<U>(pl.o_twr);
+  // the exact-add launches take the twiddles in their 12-bit form (FP32 contexts with xp)
+  const U* twh_x = pl.xp ? reinterpret_cast<const U*>(c->at<float4>(pl.o_twh12)) : twh;
+  const U* twf_x = pl.xp ? reinterpret_cast<const U*>(c->at<float4>(pl.o_twf12)) : twf;
+  const U* twr_x = pl.xp ? reinterpret_cast<const U*>(c->at<float4>(pl.o_twr12)) : twr;
   const T* axis = c->at<T>(pl.o_axis);
   const U* phase = c->at<U>(pl.o_phase);
   const C* invw = c->at<C>(pl.o_invw);
@@ -623,10 +650,10 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
     }));
   }
   if (pl.roundtrip) {
-    TRY(run(c, PSPEC_K_FFT_X, acc(2 * Sc), [&] { PT->fft_x(F0, W, twf, +1, pl.xp, s); }));
-    TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { PT->fft_y(W, 0, 1, twf, +1, c->tune.tile_y, INT_MAX, pl.xp, s); }));
+    TRY(run(c, PSPEC_K_FFT_X, acc(2 * Sc), [&] { PT->fft_x(F0, W, twf_x, +1, pl.xp, s); }));
+    TRY(run(c, PSPEC_K_FFT_Y, acc(2 * Sc), [&] { PT->fft_y(W, 0, 1, twf_x, +1, c->tune.tile_y, INT_MAX, pl.xp, s); }));
     const T scale = T(2.0 / ((double)N * N * N));
-    TRY(run(c, PSPEC_K_C2R_Z, acc(Sc + Sr), [&] { PT->c2r_z(W, f, twh, twr, scale, pl.xp, s); }));
+    TRY(run(c, PSPEC_K_C2R_Z, acc(Sc + Sr), [&] { PT->c2r_z(W, f, twh_x, twr_x, scale, pl.xp, s); }));
     transforms++;
   }
 
@@ -680,17 +707,17 @@ pspec_status do_multipoles(Ctx* c, const int32_t* ells, int n_ells, int nk, doub
                               ? c->at<float>(pl.o_rtab) + (int64_t)(ytab_base(ell) + h0 + hs) * N * N * N
                               : nullptr;
         TRY(run(c, PSPEC_K_YLM_Z, acc(Sr + Ms * Sc + (rt ? Ms * (double)N * N * N * sizeof(float) : 0.0)), [&] {
-          PT->ylm_z(f, G + hs * stride, stride, ell, h0 + hs, Ms, twh, twr, axis, rows, rt, pl.xp, s);
+          PT->ylm_z(f, G + hs * stride, stride, ell, h0 + hs, Ms, twh_x, twr_x, axis, rows, rt, pl.xp, s);
         }));
       }
       TRY(run(c, PSPEC_K_FFT_Y, acc(M * Sc * (c->frac_yr + c->frac_yw)),
-              [&] { PT->fft_y(G, stride, M, twf, -1, c->tune.tile_y, c->n2_cut, pl.xp, s); }));
+              [&] { PT->fft_y(G, stride, M, twf_x, -1, c->tune.tile_y, c->n2_cut, pl.xp, s); }));
       const float* ytab = jobs[jb].table ? jobs[jb].table + (int64_t)h0 * stride : nullptr;
       const double ybytes = ytab ? M * (double)N * N * g.NH * sizeof(float) : 0.0;
       BinArgs bj = ba;
       bj.odd = ell > 0 && (ell & 1);
       TRY(run(c, PSPEC_K_BIN_X, acc((Sc + M * Sc + ybytes) * c->frac_tile), [&] {
-        PT->bin_x(G, stride, ell, h0, M, F0, twf, jobs[jb].slot, bj, ytab ? ctas_bin : ctas_bin_plain, ytab, pl.xp, s);
+        PT->bin_x(G, stride, ell, h0, M, F0, twf_x, jobs[jb].slot, bj, ytab ? ctas_bin : ctas_bin_plain, ytab, pl.xp, s);
       }));
       transforms += M;
     }

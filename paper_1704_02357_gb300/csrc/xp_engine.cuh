@@ -6,20 +6,20 @@
 // closely a multipole of a few percent of P_0 can be recovered against a shot noise of ~80 P_0.
 //
 // Here a stage keeps every value as a pair h + l of floats:
-//   * h is a multiple of a power-of-two quantum q chosen per thread and stage, large enough
-//     that every partial sum of the stage's butterflies stays below 2^22 q. Sums and
-//     differences of such multiples are exact in FP32, so the butterfly additions of h never
-//     round.
-//   * l carries what h cannot hold: the part of a product below q and the product's own
-//     rounding error (an FMA gives it exactly). l stays within a few q, so its own roundings are
-//     ~2^-24 q, far below the rounding of the stored result.
-// A product p is put on the grid with the magic-number rounding g = (p + M) - M,
-// M = 1.5 * 2^23 q (exact for |p| < 2^22 q); p - g is then exact as well.
-//
+//   * h is a multiple of a power-of-two quantum q chosen per thread and stage from the thread's
+//     inputs, so that every value of the stage's butterflies stays below 2^11 q: h has at most
+//     12 significant bits above q. Sums and differences of such multiples are exact in FP32.
+//   * Constants and twiddles are split the same way, K = K12 + Kr with K12 a multiple of 2^-12
+//     (|K| <= 1) and Kr the remainder (held to 24 bits of its own). h * K12 then has at most 23
+//     significant bits and is exact in FP32, and so are sums of such products; h * Kr and
+//     l * K go to l, rounded at ~2^-24 q.
+//   * A product lies on the finer quantum q/4096, so before a value is multiplied again it is
+//     put back on q (re-split): g = (h + M) - M with M = 1.5 * 2^23 q rounds to q exactly and
+//     h - g is exact.
 // Values cross the shared-memory exchanges and leave the transform as h + l rounded to one
 // float, so a pass rounds each value once per exchange and once at the end, instead of once per
-// add level. Every operation whose exactness the scheme relies on uses the _rn intrinsics,
-// which the compiler never contracts into a multiply-add.
+// add level. Every operation whose exactness the scheme relies on uses the _rn intrinsics or an
+// FMA whose result is exact, and the compiler never contracts the intrinsics into a multiply-add.
 #pragma once
 #include "fft_engine.cuh"
 
@@ -36,11 +36,11 @@ __device__ __forceinline__ float xadd_(float a, float b) { return __fadd_rn(a, b
 __device__ __forceinline__ float xsub_(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float xmul_(float a, float b) { return __fmul_rn(a, b); }
 
-// M = 1.5 * 2^23 * q for the smallest power-of-two q with `bound` < 2^22 q.
+// M = 1.5 * 2^23 * q for the smallest power-of-two q with `bound` <= 2^11 q.
 __device__ __forceinline__ float xmagic(float bound) {
   int eb = (__float_as_int(bound) >> 23) & 0xff;  // bound < 2^(eb - 126)
-  eb = eb > 250 ? 250 : eb;
-  return __int_as_float(((eb + 2) << 23) | 0x400000);  // 1.5 * 2^(eb - 125)
+  eb = eb > 240 ? 240 : eb;
+  return __int_as_float(((eb + 13) << 23) | 0x400000);  // q = 2^(eb - 137), M = 1.5 * 2^(eb - 114)
 }
 __device__ __forceinline__ float xgrid(float p, float M) { return xsub_(xadd_(p, M), M); }
 
@@ -49,6 +49,12 @@ __device__ __forceinline__ xf xsplit(float v, float M) {
   return {g, xsub_(v, g)};
 }
 __device__ __forceinline__ xc xsplit(float2 v, float M) { return {xsplit(v.x, M), xsplit(v.y, M)}; }
+// back onto the quantum q before another multiplication
+__device__ __forceinline__ xf xresplit(xf a, float M) {
+  const float g = xgrid(a.h, M);
+  return {g, xadd_(a.l, xsub_(a.h, g))};
+}
+__device__ __forceinline__ xc xresplit(xc a, float M) { return {xresplit(a.x, M), xresplit(a.y, M)}; }
 __device__ __forceinline__ float xround(xf a) { return xadd_(a.h, a.l); }
 __device__ __forceinline__ float2 xround(xc a) { return make_float2(xround(a.x), xround(a.y)); }
 
@@ -60,40 +66,41 @@ __device__ __forceinline__ xc operator-(xc a, xc b) { return {a.x - b.x, a.y - b
 // a * (i * sgn)
 __device__ __forceinline__ xc xmul_i(xc a, int sgn) { return sgn > 0 ? xc{-a.y, a.x} : xc{a.y, -a.x}; }
 __device__ __forceinline__ xc xconj(xc a) { return {a.x, -a.y}; }
+__device__ __forceinline__ xf xhalf(xf a) { return {0.5f * a.h, 0.5f * a.l}; }  // exact
 
-// a * K for a constant K = hi + lo (ConstMul<float>): the exact product a.h * hi goes to the
-// grid, its remainder and rounding error, a.h * lo and a.l * K to l.
-__device__ __forceinline__ xf xcmul(xf a, const ConstMul<float>& k, float M) {
-  const float p = xmul_(a.h, k.hi);
-  const float e = fmaf(a.h, k.hi, -p);
-  const float t = fmaf(a.h, k.lo, fmaf(a.l, k.hi, e));
-  const float g = xgrid(p, M);
-  return {g, xadd_(xsub_(p, g), t)};
+// A constant |K| <= 1 as K12 (a multiple of 2^-12) + Kr, with kf = K rounded to FP32.
+struct K12 {
+  float k12, kr, kf;
+  __device__ __forceinline__ constexpr K12(double k)
+      : k12((float)((double)(long long)(k * 4096.0 + (k >= 0 ? 0.5 : -0.5)) / 4096.0)),
+        kr((float)(k - (double)(long long)(k * 4096.0 + (k >= 0 ? 0.5 : -0.5)) / 4096.0)),
+        kf((float)k) {}
+};
+// a * K; a.h on the quantum q (at most 12 significant bits): a.h * K12 is exact.
+__device__ __forceinline__ xf xcm(xf a, const K12& k) {
+  return {xmul_(a.h, k.k12), fmaf(a.l, k.kf, a.h * k.kr)};
 }
 
-// a * w for a unit twiddle w = {c_hi, s_hi, c_lo, s_lo} (tables as the plain stages use them).
-__device__ __forceinline__ xc xtw(float2 a, float4 w, float M) {
-  const float p1 = xmul_(a.x, w.x), e1 = fmaf(a.x, w.x, -p1);
-  const float p2 = xmul_(a.y, w.y), e2 = fmaf(a.y, w.y, -p2);
-  const float p3 = xmul_(a.x, w.y), e3 = fmaf(a.x, w.y, -p3);
-  const float p4 = xmul_(a.y, w.x), e4 = fmaf(a.y, w.x, -p4);
-  const float g1 = xgrid(p1, M), g2 = xgrid(p2, M), g3 = xgrid(p3, M), g4 = xgrid(p4, M);
-  const float lre = fmaf(a.x, w.z, fmaf(-a.y, w.w, xsub_(e1, e2)));
-  const float lim = fmaf(a.x, w.w, fmaf(a.y, w.z, xadd_(e3, e4)));
+// a * w for a twiddle in the 12-bit form {c12, s12, cr, sr} (tables built on the host); a on the
+// quantum q. The h parts are exact: each product has at most 23 significant bits and the FMA's
+// exact result is representable.
+__device__ __forceinline__ xc xtw(xc a, float4 w) {
+  const float cf = xadd_(w.x, w.z), sf = xadd_(w.y, w.w);
   xc r;
-  r.x = {xsub_(g1, g2), xadd_(xsub_(xsub_(p1, g1), xsub_(p2, g2)), lre)};
-  r.y = {xadd_(g3, g4), xadd_(xadd_(xsub_(p3, g3), xsub_(p4, g4)), lim)};
+  r.x.h = fmaf(a.x.h, w.x, -xmul_(a.y.h, w.y));
+  r.y.h = fmaf(a.x.h, w.y, xmul_(a.y.h, w.x));
+  r.x.l = fmaf(a.x.l, cf, fmaf(-a.y.l, sf, fmaf(a.x.h, w.z, -(a.y.h * w.w))));
+  r.y.l = fmaf(a.x.l, sf, fmaf(a.y.l, cf, fmaf(a.x.h, w.w, a.y.h * w.z)));
   return r;
 }
-__device__ __forceinline__ xc xtw(xc a, float4 w, float M) {
-  xc r = xtw(make_float2(a.x.h, a.y.h), w, M);
-  r.x.l = fmaf(a.x.l, w.x, fmaf(-a.y.l, w.y, r.x.l));
-  r.y.l = fmaf(a.x.l, w.y, fmaf(a.y.l, w.x, r.y.l));
-  return r;
-}
+__device__ __forceinline__ xc xtw(float2 a, float4 w, float M) { return xtw(xsplit(a, M), w); }
+// conjugate twiddle (inverse transforms)
+__device__ __forceinline__ float4 xconj_w(float4 w) { return make_float4(w.x, -w.y, w.z, -w.w); }
 
 // ------------------------------------------------------------------ butterflies
-// The radix-R DFTs of common.cuh (same decompositions and constants) on exact-add values.
+// The radix-R DFTs of common.cuh (same decompositions and constants) on exact-add values. The
+// inputs may lie on the finer quantum (twiddled): a value is re-split before each internal
+// multiplication.
 template <int R> struct XDft;
 
 template <> struct XDft<2> {
@@ -117,25 +124,25 @@ template <> struct XDft<4> {
 };
 
 // z * (sr cr + i si ci) with sr, si = +-1
-__device__ __forceinline__ xc xrot(xc z, const ConstMul<float>& cr, const ConstMul<float>& ci, int sr, int si,
-                                   float M) {
-  const xf ax = xcmul(z.x, cr, M), ay = xcmul(z.y, ci, M);  // cr z.x, ci z.y
-  const xf bx = xcmul(z.y, cr, M), by = xcmul(z.x, ci, M);  // cr z.y, ci z.x
+__device__ __forceinline__ xc xrot(xc z, const K12& cr, const K12& ci, int sr, int si, float M) {
+  z = xresplit(z, M);
+  const xf ax = xcm(z.x, cr), ay = xcm(z.y, ci);  // cr z.x, ci z.y
+  const xf bx = xcm(z.y, cr), by = xcm(z.x, ci);  // cr z.y, ci z.x
   const xf p = sr > 0 ? ax : -ax, q = si > 0 ? ay : -ay;
   const xf s = sr > 0 ? bx : -bx, u = si > 0 ? by : -by;
   return {p - q, s + u};
 }
 // z * (sgn + dir i) / sqrt2 (sgn = +-1)
-__device__ __forceinline__ xc xdiag(xc z, int sgn, int dir, const ConstMul<float>& h, float M) {
+__device__ __forceinline__ xc xdiag(xc z, int sgn, int dir, const K12& h, float M) {
   const xf zx = sgn > 0 ? z.x : -z.x, zy = sgn > 0 ? z.y : -z.y;
   const xf re = dir > 0 ? zx - z.y : zx + z.y;  // sgn z.x - dir z.y
   const xf im = dir > 0 ? zy + z.x : zy - z.x;  // sgn z.y + dir z.x
-  return {xcmul(re, h, M), xcmul(im, h, M)};
+  return {xcm(xresplit(re, M), h), xcm(xresplit(im, M), h)};
 }
 
 template <> struct XDft<8> {
   static __device__ __forceinline__ void run(xc* v, int dir, float M) {
-    const ConstMul<float> h(0.70710678118654752440);
+    const K12 h(0.70710678118654752440);
     xc e[4] = {v[0], v[2], v[4], v[6]};
     xc o[4] = {v[1], v[3], v[5], v[7]};
     XDft<4>::run(e, dir, M);
@@ -156,7 +163,7 @@ template <> struct XDft<8> {
 
 template <> struct XDft<16> {
   static __device__ __forceinline__ void run(xc* v, int dir, float M) {
-    const ConstMul<float> h(0.70710678118654752440), c1(0.92387953251128675613), s1(0.38268343236508977173);
+    const K12 h(0.70710678118654752440), c1(0.92387953251128675613), s1(0.38268343236508977173);
     xc a[4][4];
 #pragma unroll
     for (int n2 = 0; n2 < 4; n2++) {
@@ -185,40 +192,13 @@ template <> struct XDft<16> {
   }
 };
 
-template <> struct XDft<32> {
-  static __device__ __forceinline__ void run(xc* v, int dir, float M) {
-    xc e[16], o[16];
-#pragma unroll
-    for (int i = 0; i < 16; i++) {
-      e[i] = v[2 * i];
-      o[i] = v[2 * i + 1];
-    }
-    XDft<16>::run(e, dir, M);
-    XDft<16>::run(o, dir, M);
-    constexpr double kc[9] = {1.0, 0.98078528040323044913, 0.92387953251128675613, 0.83146961230254523708,
-                              0.70710678118654752440, 0.55557023301960222474, 0.38268343236508977173,
-                              0.19509032201612826785, 0.0};
-#pragma unroll
-    for (int k = 0; k < 16; k++) {
-      xc w = o[k];
-      if (k > 0) {
-        const int kk = k <= 8 ? k : 16 - k;
-        const ConstMul<float> cr(kc[kk]), ci(kc[8 - kk]);
-        w = xrot(w, cr, ci, k <= 8 ? 1 : -1, dir, M);
-      }
-      v[k] = e[k] + w;
-      v[k + 16] = e[k] - w;
-    }
-  }
-};
-
 template <> struct XDft<3> {
   static __device__ __forceinline__ void run(xc* v, int dir, float M) {
-    const ConstMul<float> s3(0.86602540378443864676), half(0.5);
+    const K12 s3(0.86602540378443864676);
     const xc t = v[1] + v[2];
-    const xc u = v[1] - v[2];
-    const xc m = v[0] - xc{xcmul(t.x, half, M), xcmul(t.y, half, M)};
-    const xf sx = xcmul(u.x, s3, M), sy = xcmul(u.y, s3, M);
+    const xc u = xresplit(v[1] - v[2], M);
+    const xc m = v[0] - xc{xhalf(t.x), xhalf(t.y)};
+    const xf sx = xcm(u.x, s3), sy = xcm(u.y, s3);
     const xc isu = dir > 0 ? xc{-sy, sx} : xc{sy, -sx};  // i dir sin(2 pi/3) u
     v[0] = v[0] + t;
     v[1] = m + isu;
@@ -249,7 +229,7 @@ __device__ __forceinline__ void stage_xp(float2 (&v)[E], float2* sm, int t, int 
   float bound = 0.f;
 #pragma unroll
   for (int e = 0; e < E; e++) bound += fabsf(v[e].x) + fabsf(v[e].y);
-  const float M = xmagic(2.f * bound);
+  const float M = xmagic(2.f * bound);  // twice: a rotated component reaches sqrt2 |x|
 #pragma unroll
   for (int q = 0; q < Q; q++) {
     const int j = t + Tc * q;
@@ -265,7 +245,7 @@ __device__ __forceinline__ void stage_xp(float2 (&v)[E], float2* sm, int t, int 
           w = ldg_u(tw + r * k * TSTEP);
           if (DIR > 0) w = uconj(w);
         }
-        u[r] = xtw(v[q + r * Q], w, M);
+        u[r] = xtw(v[q + r * Q], w, M);  // the 12-bit twiddle table
       } else {
         u[r] = xsplit(v[q + r * Q], M);
       }
@@ -311,24 +291,24 @@ __device__ __forceinline__ void fft_any(C (&v)[E], C* sm, int t, int seq, const 
 }
 
 // r2c unpack (k_r2c_z) in exact-add arithmetic: 2X[k] = (Z[k] + Z*[L-k]) - i w^k (Z[k] - Z*[L-k]),
-// halved once at the end (exact).
+// halved once at the end (exact); w in the 12-bit form.
 __device__ __forceinline__ float2 r2c_unpack_xp(float2 zk, float2 zm, float4 w) {
   const float bound = fabsf(zk.x) + fabsf(zk.y) + fabsf(zm.x) + fabsf(zm.y);
   const float M = xmagic(4.f * bound);
   const xc a = xsplit(zk, M), b = xconj(xsplit(zm, M));
   const xc s = a + b, d = a - b;
-  const xc o = xtw(xc{d.y, -d.x}, w, M);  // -i d w
+  const xc o = xtw(xc{d.y, -d.x}, w);  // -i d w
   const float2 r = xround(s + o);
   return make_float2(0.5f * r.x, 0.5f * r.y);
 }
 
-// c2r pack (k_c2r_z) in exact-add arithmetic: Z = E + i O with 2E = X[k] + X*[L-k] and
-// 2O = i conj(w^k) (X[k] - X*[L-k]) -> 2Z = (X[k] + X*[L-k]) - conj(w^k) (X[k] - X*[L-k]) ... halved at the end.
+// c2r pack (k_c2r_z) in exact-add arithmetic: with A = X[k] and B = conj(X[L-k]) (0 for k = 0),
+// 2Z = (A + B) + i (A - B) conj(w^k), halved once at the end; wc = conj(w^k) in the 12-bit form.
 __device__ __forceinline__ float2 c2r_pack_xp(float2 xk, float2 xm, float4 wc) {
   const float bound = fabsf(xk.x) + fabsf(xk.y) + fabsf(xm.x) + fabsf(xm.y);
   const float M = xmagic(4.f * bound);
   const xc a = xsplit(xk, M), b = xconj(xsplit(xm, M));
-  const xc ev = a + b, od = xtw(a - b, wc, M);  // 2E, 2O' = (X - X*) conj(w)
+  const xc ev = a + b, od = xtw(a - b, wc);
   const float2 r = xround(xc{ev.x - od.y, ev.y + od.x});  // 2E + i 2O'
   return make_float2(0.5f * r.x, 0.5f * r.y);
 }
