@@ -308,8 +308,14 @@ __global__ void __launch_bounds__(ylm_thread_cap(LT), sizeof(T) == 4 ? ylm_min_b
 // XP: exact-add stages (FP32 only).
 template <int N, bool XP> constexpr int col_elems() { return XP ? Shape<N>::EYX : Shape<N>::EY; }
 
+// Exact-add blocks of 256 threads: three per SM (80 registers) beat two (104), measured.
+template <int N, bool XP> constexpr int y_min_blocks(int threads) {
+  return XP && threads == 256 ? 3 : min_blocks<float, col_elems<N, XP>()>(threads);
+}
 template <typename T, int N, int DIR, int TW, bool XP>
-__global__ void __launch_bounds__(TW * (N / col_elems<N, XP>()), min_blocks<T, col_elems<N, XP>()>(TW * (N / col_elems<N, XP>())))
+__global__ void __launch_bounds__(TW * (N / col_elems<N, XP>()),
+                                  sizeof(T) == 4 ? y_min_blocks<N, XP>(TW * (N / col_elems<N, XP>()))
+                                                 : min_blocks<T, col_elems<N, XP>()>(TW * (N / col_elems<N, XP>())))
     k_fft_y(cx<T>* __restrict__ data, int64_t spec_stride, const ux<T>* __restrict__ twf, int n2_cut) {
   using C = cx<T>;
   using S = Shape<N>;
