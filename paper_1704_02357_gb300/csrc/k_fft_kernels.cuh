@@ -196,19 +196,30 @@ __global__ void __launch_bounds__(ylm_thread_cap(LT), sizeof(T) == 4 ? ylm_min_b
   C* xb = reinterpret_cast<C*>(smraw);
   const int row0 = blockIdx.x * rows;
   const int a_lo = LT < 0 ? 0 : harm_a(h0), a_hi = LT < 0 ? 0 : harm_a(h0 + M - 1);
+  if constexpr (sizeof(T) == 4 && LT >= 0) {
+    if (rtab) {
+      // Y_lm(rhat) from the table (harmonics h0.., one slot of N^3 nodes each): each thread takes
+      // one 4-node vector of one row, loads f once and the M table vectors back to back
+      constexpr int64_t pts = (int64_t)N * N * N;
+      constexpr int NV = N / 4;
+      for (int q = threadIdx.x; q < rows * NV; q += blockDim.x) {
+        const int r = q / NV, kv = q - r * NV;
+        const int64_t at = (int64_t)(row0 + r) * N + 4 * kv;
+        const float4 fv = __ldg(reinterpret_cast<const float4*>(f + at));
+        const float* trow = rtab + at;
+#pragma unroll 4
+        for (int s = 0; s < M; s++) {
+          const float4 y = __ldg(reinterpret_cast<const float4*>(trow + s * pts));
+          *reinterpret_cast<float4*>(stage + (s * rows + r) * N + 4 * kv) =
+              make_float4(fv.x * y.x, fv.y * y.y, fv.z * y.z, fv.w * y.w);
+        }
+      }
+    }
+  }
   for (int r = 0; r < rows; r++) {
     const int grow = row0 + r;
     if constexpr (sizeof(T) == 4 && LT >= 0) {
-      if (rtab) {  // Y_lm(rhat) from the table (harmonics h0.., one slot of N^3 nodes each)
-        constexpr int64_t pts = (int64_t)N * N * N;
-        const T* frow = f + (int64_t)grow * N;
-        const float* trow = rtab + (int64_t)grow * N;
-        for (int kk = threadIdx.x; kk < N; kk += blockDim.x) {
-          const T fv = frow[kk];
-          for (int s = 0; s < M; s++) stage[(s * rows + r) * N + kk] = fv * __ldg(trow + s * pts + kk);
-        }
-        continue;
-      }
+      if (rtab) continue;
     }
     const int i = grow / N, j = grow - i * N;
     const T vx = axis[i], vy = axis[N + j];
