@@ -91,18 +91,28 @@ template <> const YTab<double>& host_ytab<double>() {
 }
 
 // ------------------------------------------------------------------ Y_lm(khat) table
+// Position m of a k-space table of the binning pass -> its mode (i, j, kz): one block of N x tw
+// values per x tile (j, kz tile), rows i, m = ((kz / tw * N + j) * N + i) * tw + kz % tw.
+__device__ __forceinline__ void table_mode(int64_t m, int N, int tw, int& i, int& j, int& kz) {
+  const int c = (int)(m % tw);
+  int64_t r = m / tw;
+  i = (int)(r % N);
+  r /= N;
+  j = (int)(r % N);
+  kz = (int)(r / N) * tw + c;
+}
+
 // One thread per stored mode (i, j, kz): khat in FP64, then for a = 0..l_max the recurrence in
 // l (FP64 coefficients) and (x + i y)^a; each Y_{l,m} of an even l >= 2 is stored rounded to
-// FP32 at ytab[(ytab_base(l) + h) * modes + (i N + j) NH + kz] (h = 0, 2a-1, 2a for m = 0,
-// +a, -a). The mode k = 0 gets 0.
-__global__ void __launch_bounds__(256) k_ytab_build(float* __restrict__ ytab, int N, int ell_max,
+// FP32 at ytab[(ytab_base(l) + h) * modes + m] (h = 0, 2a-1, 2a for m = 0, +a, -a; m the
+// table position of the mode). The mode k = 0 gets 0.
+__global__ void __launch_bounds__(256) k_ytab_build(float* __restrict__ ytab, int N, int tw, int ell_max,
                                                     const __grid_constant__ YTab<double> yt) {
   const int NH = N / 2;
   const int64_t modes = (int64_t)N * N * NH;
   for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < modes; m += (int64_t)gridDim.x * blockDim.x) {
-    const int kz = (int)(m % NH);
-    const int64_t ij = m / NH;
-    const int j = (int)(ij % N), i = (int)(ij / N);
+    int i, j, kz;
+    table_mode(m, N, tw, i, j, kz);
     const double fx = i < NH ? i : i - N, fy = j < NH ? j : j - N, fz = kz;
     const double r2 = fx * fx + fy * fy + fz * fz;
     const double inv = r2 > 0.0 ? 1.0 / sqrt(r2) : 0.0;
@@ -192,19 +202,18 @@ void launch_rtab_build(float* rtab, int N, int ell_max, const RGeo& g, int nsm, 
   k_rtab_build<<<8 * nsm, 256, 0, s>>>(rtab, N, ell_max, g, host_ytab<double>());
 }
 
-void launch_ytab_build(float* ytab, int N, int ell_max, int nsm, cudaStream_t s) {
-  k_ytab_build<<<8 * nsm, 256, 0, s>>>(ytab, N, ell_max, host_ytab<double>());
+void launch_ytab_build(float* ytab, int N, int tw, int ell_max, int nsm, cudaStream_t s) {
+  k_ytab_build<<<8 * nsm, 256, 0, s>>>(ytab, N, tw, ell_max, host_ytab<double>());
 }
 
-// Cartesian k-space factors: ctab[q * modes + (i N + j) NH + kz] = mult_q khat^q in FP64,
-// rounded once to FP32 (0 for k = 0).
-__global__ void __launch_bounds__(256) k_ctab_build(float* __restrict__ ctab, int N) {
+// Cartesian k-space factors: ctab[q * modes + m] = mult_q khat^q in FP64, rounded once to FP32
+// (0 for k = 0), m the table position of the mode.
+__global__ void __launch_bounds__(256) k_ctab_build(float* __restrict__ ctab, int N, int tw) {
   const int NH = N / 2;
   const int64_t modes = (int64_t)N * N * NH;
   for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < modes; m += (int64_t)gridDim.x * blockDim.x) {
-    const int kz = (int)(m % NH);
-    const int64_t ij = m / NH;
-    const int j = (int)(ij % N), i = (int)(ij / N);
+    int i, j, kz;
+    table_mode(m, N, tw, i, j, kz);
     const double fx = i < NH ? i : i - N, fy = j < NH ? j : j - N, fz = kz;
     const double r2 = fx * fx + fy * fy + fz * fz;
     const double inv = r2 > 0.0 ? 1.0 / sqrt(r2) : 0.0;
@@ -217,7 +226,9 @@ __global__ void __launch_bounds__(256) k_ctab_build(float* __restrict__ ctab, in
   }
 }
 
-void launch_ctab_build(float* ctab, int N, int nsm, cudaStream_t s) { k_ctab_build<<<8 * nsm, 256, 0, s>>>(ctab, N); }
+void launch_ctab_build(float* ctab, int N, int tw, int nsm, cudaStream_t s) {
+  k_ctab_build<<<8 * nsm, 256, 0, s>>>(ctab, N, tw);
+}
 
 // ------------------------------------------------------------------ dispatch
 template <typename T> const PassTable<T>* pass_table(int N) {

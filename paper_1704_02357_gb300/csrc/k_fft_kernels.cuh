@@ -3,17 +3,17 @@
 // as templates on the mesh side N; each supported N is instantiated in its own translation
 // unit (pass_<N>.cu) and reached through a PassTable.
 //
-// Storage: real mesh r[(i*N + j)*N + k]; half spectrum s[(i*N + j)*NH + kz], NH = N/2.
-// The kz = N/2 plane is never stored: its modes are zeroed before the inverse transform
-// and never binned, so nothing downstream reads it.
+// Storage: real mesh r[(i*N + j)*N + k]; half spectrum (NH = N/2 stored kz) in kz tiles of TW
+// modes, each tile an (i, j) plane of TW-mode rows (Lay below). The kz = N/2 plane is never
+// stored: its modes are zeroed before the inverse transform and never binned, so nothing
+// downstream reads it.
 //
 // A 3-D forward transform is three passes, each one HBM round trip:
 //   z: rows of N reals -> N/2-point complex FFT of packed pairs -> unpack to N/2 modes
 //   y: columns along j of an (i, kz-tile) slab, in place
 //   x: columns along i of a (j, kz-tile) slab; fused with the interlace/compensate
 //      combine (F0 and the l = 0 sums) or with the Y_lm(khat) accumulate-and-bin.
-// Every pass keeps its elements in registers (fft_engine.cuh); kz tiles of TW columns give
-// TW*8-byte contiguous segments per row.
+// Every pass keeps its elements in registers (fft_engine.cuh).
 #pragma once
 #include <cmath>
 #include "launch.h"
@@ -55,6 +55,24 @@ template <int N, bool XP> struct ZShape {
   static constexpr bool ZW = Tz <= 32;
   static constexpr int ROWS = (S::ROWS * S::Tz / Tz) > 0 ? (S::ROWS * S::Tz / Tz) : 1;
   static constexpr int ZT = ROWS * Tz;
+};
+
+// ------------------------------------------------------------------ spectrum storage order
+// s[((kz / TW * N + i) * N + j) * TW + kz % TW]: a y-pass slab (i, kz tile) is one contiguous
+// block, an x-pass tile (j, kz tile) is N rows of TW modes N*TW modes apart, and a z-pass block
+// of consecutive rows writes a run of rows*TW modes into each kz tile. (With rows of TW modes
+// N*N/2 modes apart, the order of rows along kz, the x passes ran at about 3/4 of this order's
+// bandwidth: the requests of the concurrent tiles fell into too few DRAM channels.)
+template <int N> struct Lay {
+  static constexpr int TW = Shape<N>::TW;
+  static constexpr int64_t KT = (int64_t)N * N * TW;  // between kz tiles
+  static constexpr int64_t XI = (int64_t)N * TW;      // between i: the x passes' element stride
+  static constexpr int64_t YJ = TW;                   // between j: the y pass's element stride
+  // mode kz of z-pass row r = i N + j
+  __device__ static __forceinline__ int64_t row(int64_t r, int kz) { return (int64_t)(kz / TW) * KT + r * TW + kz % TW; }
+  __device__ static __forceinline__ int64_t at(int i, int j, int kz) { return row((int64_t)i * N + j, kz); }
+  // first mode of the k-space table block of x tile (j, kz tile kt); element (i, c) at + i TW + c
+  __device__ static __forceinline__ int64_t table_tile(int kt, int j) { return ((int64_t)kt * N + j) * N * TW; }
 };
 
 // Resident blocks per SM the register allocation must allow. Threads holding 24 complex
@@ -132,11 +150,10 @@ __global__ void __launch_bounds__(Shape<N>::ZT, min_blocks<T, Shape<N>::EZ>(Shap
       zm[e] = sm[sidx<kPaddedRows, L, 1>(r, k ? L - k : 0)];
     }
   }
-  C* dst = out + (int64_t)row * L;
 #pragma unroll
   for (int e = 0; e < E; e++) {
     const int k = t + Tc * e;
-    dst[k] = r2c_unpack<C, T>(v[e], zm[e], ldg_u(twr + k));
+    out[Lay<N>::row(row, k)] = r2c_unpack<C, T>(v[e], zm[e], ldg_u(twr + k));
   }
 }
 
@@ -154,16 +171,15 @@ __global__ void __launch_bounds__(ZShape<N, XP>::ZT, min_blocks<T, ZShape<N, XP>
   C* sm = reinterpret_cast<C*>(smraw);
   const int r = threadIdx.x / Tc, t = threadIdx.x - r * Tc;
   const int row = blockIdx.x * S::ROWS + r;
-  const C* src = in + (int64_t)row * L;
   C v[E];
 #pragma unroll
   for (int e = 0; e < E; e++) {
     const int k = t + Tc * e;
-    const C xk = src[k];
+    const C xk = in[Lay<N>::row(row, k)];
     if constexpr (XP) {
-      v[e] = c2r_pack_xp(xk, k ? src[L - k] : mk(T(0), T(0)), uconj(ldg_u(twr + k)));
+      v[e] = c2r_pack_xp(xk, k ? in[Lay<N>::row(row, L - k)] : mk(T(0), T(0)), uconj(ldg_u(twr + k)));
     } else {
-      const C xm = k ? cconj(src[L - k]) : mk(T(0), T(0));
+      const C xm = k ? cconj(in[Lay<N>::row(row, L - k)]) : mk(T(0), T(0));
       const C ev = cscale(cadd(xk, xm), T(0.5));
       const C od = umul(cscale(csub(xk, xm), T(0.5)), uconj(ldg_u(twr + k)));
       v[e] = mk(ev.x - od.y, ev.y + od.x);  // E + i O
@@ -179,8 +195,9 @@ __global__ void __launch_bounds__(ZShape<N, XP>::ZT, min_blocks<T, ZShape<N, XP>
 // For `rows` rows of f and the M harmonics h0..h0+M-1 of multipole l. Every point sweeps
 // its harmonics once ((x+iy)^a carried from one |m| to the next) into a shared staging
 // area of nseq = M*rows real rows; then each of the nseq*Tz threads loads its slots, the
-// sequences are transformed (the staging area is reused as the exchange buffer) and
-// unpacked into the M spectra.
+// sequences are transformed (each sequence's staging row is its exchange row) and unpacked
+// into the M spectra. With the Y_lm(rhat) table and sequences within one warp, each warp
+// stages its own sequences, and the pass runs without block barriers.
 template <typename T, int N, int LT, bool XP>
 __global__ void __launch_bounds__(ylm_thread_cap(LT), sizeof(T) == 4 ? ylm_min_blocks(LT, XP) : 0) k_ylm_r2c_z(const T* __restrict__ f, cx<T>* __restrict__ out,
                                                   int64_t spec_stride, int ell, int h0, int M,
@@ -192,11 +209,33 @@ __global__ void __launch_bounds__(ylm_thread_cap(LT), sizeof(T) == 4 ? ylm_min_b
   using S = ZShape<N, XP>;
   constexpr int L = N / 2, E = S::E, Tc = S::Tz;
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* stage = reinterpret_cast<T*>(smraw);  // [nseq][N] reals, then the exchange buffer
+  // staging stride in reals: N, or (warp-local staging) one exchange row, so that a sequence's
+  // staging row is its own exchange row
+  constexpr int SP = 2 * padded_len(L);
+  T* stage = reinterpret_cast<T*>(smraw);  // [nseq][N or SP] reals, then the exchange buffer
   C* xb = reinterpret_cast<C*>(smraw);
   const int row0 = blockIdx.x * rows;
   const int a_lo = LT < 0 ? 0 : harm_a(h0), a_hi = LT < 0 ? 0 : harm_a(h0 + M - 1);
-  if constexpr (sizeof(T) == 4 && LT >= 0) {
+  const int sq = threadIdx.x / Tc, t = threadIdx.x - sq * Tc;
+  constexpr bool kWarpTable = sizeof(T) == 4 && LT >= 0 && S::ZW && SP % 4 == 0;  // 16-byte rows
+  const bool warp_local = kWarpTable && rtab != nullptr;  // uniform over the block
+  if constexpr (kWarpTable) {
+    if (rtab) {
+      // the Tc threads of sequence (s, r) stage f * Y_lm(rhat) of their own row, 4 nodes a step
+      constexpr int64_t pts = (int64_t)N * N * N;
+      constexpr int NV = N / 4;
+      const int s = sq / rows, r = sq - s * rows;
+      const int64_t at0 = (int64_t)(row0 + r) * N;
+      const float4* fr = reinterpret_cast<const float4*>(f + at0);
+      const float4* yr = reinterpret_cast<const float4*>(rtab + (int64_t)s * pts + at0);
+      float4* dr = reinterpret_cast<float4*>(stage + sq * SP);
+#pragma unroll 4
+      for (int kv = t; kv < NV; kv += Tc) {
+        const float4 fv = __ldg(fr + kv), y = __ldg(yr + kv);
+        dr[kv] = make_float4(fv.x * y.x, fv.y * y.y, fv.z * y.z, fv.w * y.w);
+      }
+    }
+  } else if constexpr (sizeof(T) == 4 && LT >= 0) {
     if (rtab) {
       // Y_lm(rhat) from the table (harmonics h0.., one slot of N^3 nodes each): each thread takes
       // one 4-node vector of one row, loads f once and the M table vectors back to back
@@ -287,33 +326,41 @@ __global__ void __launch_bounds__(ylm_thread_cap(LT), sizeof(T) == 4 ? ylm_min_b
       }
     }
   }
-  __syncthreads();
+  if (warp_local)
+    __syncwarp();
+  else
+    __syncthreads();
   const C* stc = reinterpret_cast<const C*>(stage);
-  const int sq = threadIdx.x / Tc, t = threadIdx.x - sq * Tc;
   C v[E];
 #pragma unroll
-  for (int e = 0; e < E; e++) v[e] = stc[sq * L + t + Tc * e];
-  __syncthreads();
+  for (int e = 0; e < E; e++) v[e] = stc[sq * (warp_local ? SP / 2 : L) + t + Tc * e];
+  // the staging area becomes the exchange buffer: a sequence's own row (warp-local), else shared
+  if (warp_local)
+    __syncwarp();
+  else
+    __syncthreads();
   fft_any<XP, C, E, L, kPaddedRows, 1, -1, S::ZW>(v, xb, t, sq, twh);
   // mirrors through shared memory (shuffles would raise this kernel's register count, measured slower)
 #pragma unroll
   for (int e = 0; e < E; e++) xb[sidx<kPaddedRows, L, 1>(sq, t + Tc * e)] = v[e];
   fft_sync<S::ZW>();
   const int s = sq / rows, r = sq - s * rows;
-  C* dst = out + s * spec_stride + (int64_t)(row0 + r) * L;
+  C* dst = out + s * spec_stride;
+  const int64_t grow = row0 + r;
 #pragma unroll
   for (int e = 0; e < E; e++) {
     const int k = t + Tc * e;
     const C zm = xb[sidx<kPaddedRows, L, 1>(sq, k ? L - k : 0)];
     if constexpr (XP)
-      dst[k] = r2c_unpack_xp(v[e], zm, ldg_u(twr + k));
+      dst[Lay<N>::row(grow, k)] = r2c_unpack_xp(v[e], zm, ldg_u(twr + k));
     else
-      dst[k] = r2c_unpack<C, T>(v[e], zm, ldg_u(twr + k));
+      dst[Lay<N>::row(grow, k)] = r2c_unpack<C, T>(v[e], zm, ldg_u(twr + k));
   }
 }
 
 // ------------------------------------------------------------------ pass y (in place)
-// Block: one (i, kz-tile) slab, TW columns x Tc threads (column fastest). Outputs (ky, kz)
+// Block: one (i, kz-tile) slab, TW columns x Tc threads (column fastest); blocks in storage
+// order (kz tile, i, part of the tile when TW is a fraction of the storage tile). Outputs (ky, kz)
 // with ky^2 + kz^2 >= n2_cut are not stored: every mode of their x column lies beyond the
 // last bin, and the binning pass skips those columns (INT_MAX stores everything).
 // XP: exact-add stages (FP32 only).
@@ -333,20 +380,22 @@ __global__ void __launch_bounds__(TW * (N / col_elems<N, XP>()),
   constexpr int NH = S::NH, E = col_elems<N, XP>(), Tc = N / E;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
+  static_assert(Lay<N>::TW % TW == 0, "a y tile lies within one storage tile");
+  constexpr int SUB = Lay<N>::TW / TW;
   const int c = threadIdx.x % TW, t = threadIdx.x / TW;
-  constexpr int ntz = NH / TW;
-  const int i = blockIdx.x / ntz, kz0 = (blockIdx.x - i * ntz) * TW;
+  const int part = blockIdx.x % SUB, slab = blockIdx.x / SUB, kt = slab / N, i = slab - kt * N;
+  const int kz0 = kt * Lay<N>::TW + part * TW;
   if (kz0 * kz0 >= n2_cut) return;  // the whole slab is beyond the last bin (uniform per block)
   const int kz = kz0 + c;
-  C* base = data + (int64_t)blockIdx.y * spec_stride + (int64_t)i * N * NH + kz;
+  C* base = data + (int64_t)blockIdx.y * spec_stride + Lay<N>::at(i, 0, kz);
   C v[E];
 #pragma unroll
-  for (int e = 0; e < E; e++) v[e] = base[(int64_t)(t + Tc * e) * NH];
+  for (int e = 0; e < E; e++) v[e] = base[(int64_t)(t + Tc * e) * Lay<N>::YJ];
   fft_any<XP, C, E, N, kInterleaved, TW, DIR>(v, sm, t, c, twf);
 #pragma unroll
   for (int e = 0; e < E; e++) {
     const int ny = sfreq<N>(t + Tc * e);
-    if (ny * ny + kz * kz < n2_cut) base[(int64_t)(t + Tc * e) * NH] = v[e];
+    if (ny * ny + kz * kz < n2_cut) base[(int64_t)(t + Tc * e) * Lay<N>::YJ] = v[e];
   }
 }
 
@@ -361,10 +410,9 @@ __global__ void __launch_bounds__(Shape<N>::TW * (N / col_elems<N, XP>()),
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int c = threadIdx.x % TW, t = threadIdx.x / TW;
-  constexpr int ntz = NH / TW;
-  const int j = blockIdx.x / ntz, kz0 = (blockIdx.x - j * ntz) * TW;
-  constexpr int64_t si = (int64_t)N * NH;
-  const int64_t off = (int64_t)j * NH + kz0 + c;
+  const int kt = blockIdx.x / N, j = blockIdx.x - kt * N;  // tiles in storage order
+  constexpr int64_t si = Lay<N>::XI;
+  const int64_t off = Lay<N>::at(0, j, kt * TW + c);
   C v[E];
 #pragma unroll
   for (int e = 0; e < E; e++) v[e] = in[off + (t + Tc * e) * si];
@@ -393,13 +441,13 @@ __global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T, Shape<N>::E>(Shape
   wb.w = reinterpret_cast<T*>(wb.b + ba.nk);
   wb.init();
   const int c = threadIdx.x % TW, t = threadIdx.x / TW;
-  constexpr int ntz = NH / TW, ntiles = N * ntz;
-  constexpr int64_t si = (int64_t)N * NH;
+  constexpr int ntiles = N * (NH / TW);
+  constexpr int64_t si = Lay<N>::XI;
   __syncthreads();
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int j = tile / ntz, kz0 = (tile - j * ntz) * TW;
-    const int kz = kz0 + c;
-    const int64_t off = (int64_t)j * NH + kz;
+    const int kt = tile / N, j = tile - kt * N;  // tiles in storage order
+    const int kz = kt * TW + c;
+    const int64_t off = Lay<N>::at(0, j, kz);
     C v[E];
 #pragma unroll
     for (int e = 0; e < E; e++) v[e] = B[off + (t + Tc * e) * si];
@@ -472,14 +520,13 @@ __global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T, Shape<N>::E>(Shape
   wb.w = reinterpret_cast<T*>(wb.b + ba.nk);
   wb.init();
   const int c = threadIdx.x % TW, t = threadIdx.x / TW;
-  constexpr int ntz = NH / TW;
-  constexpr int64_t si = (int64_t)N * NH;
+  constexpr int64_t si = Lay<N>::XI, modes = (int64_t)N * N * NH;
   __syncthreads();
   for (int q = blockIdx.x; q < ba.n_xtiles; q += gridDim.x) {
     const int tile = ba.xtiles[q];
-    const int j = tile / ntz, kz0 = (tile - j * ntz) * TW;
-    const int kz = kz0 + c;
-    const int64_t off = (int64_t)j * NH + kz;
+    const int kt = tile / N, j = tile - kt * N;  // x tiles in storage order
+    const int kz = kt * TW + c;
+    const int64_t off = Lay<N>::at(0, j, kz);
     const T fy = T(sfreq<N>(j)), fz = T(kz);
     const T r2yz = fy * fy + fz * fz;
     T acc[E];
@@ -492,14 +539,14 @@ __global__ void __launch_bounds__(Shape<N>::CT, min_blocks<T, Shape<N>::E>(Shape
       const int h = h0 + s;
       const int a = harm_a(h), sg = harm_sign(h);
       const C* Gs = G + (int64_t)s * spec_stride;
-      // FP32 with a table: Y_lm(khat) of this harmonic, same mode layout as the spectra
-      const float* Ys = YT ? ytab + (int64_t)s * (si * N) + off : nullptr;
+      // FP32 with a table: Y_lm(khat) of this harmonic, one contiguous block per x tile
+      const float* Ys = YT ? ytab + (int64_t)s * modes + Lay<N>::table_tile(kt, j) + c : nullptr;
       C v[E];
       float yv[YT ? E : 1];  // table values, loaded with the spectrum so that the FFT hides their latency
 #pragma unroll
       for (int e = 0; e < E; e++) {
         v[e] = Gs[off + (t + Tc * e) * si];
-        if constexpr (YT) yv[e] = __ldg(Ys + (t + Tc * e) * si);
+        if constexpr (YT) yv[e] = __ldg(Ys + (t + Tc * e) * TW);
       }
       fft_any<XP, C, E, N, kInterleaved, TW, -1>(v, sm, t, c, twf);
 #pragma unroll
@@ -566,11 +613,13 @@ template <int NPEND> __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory");
 }
 
-// The binning pass of the FP32 path with the Y_lm(khat) table. While harmonic s is
-// transformed, the G tile and the Y tile of harmonic s+1 are copied asynchronously into the
-// other half of a double buffer, so the x pass no longer waits on global loads; the landed G
-// tile also serves as the transform's exchange buffer, and F0 stays in registers (each thread
-// owns its modes for the whole tile).
+// The binning pass of the FP32 path with the Y_lm(khat) table, as one stream of copy stages
+// per block: for each of its x tiles the M harmonic stages (the G tile and the Y_lm(khat) tile
+// of harmonic h0 + k), then the F0 tile. While one stage is used, the next one (of the same
+// tile, or the first of the block's next tile) is copied asynchronously into the other half of
+// a double buffer, so neither the x pass nor a new tile waits on global loads. A landed G tile
+// serves as its transform's exchange buffer. Each thread keeps S = sum_h Y_h Ghat_h over its
+// modes (Ghat the x-transformed G), and F0 enters once per tile: Re[S conj(F0)].
 template <int N, bool XP>
 __global__ void __launch_bounds__(Shape<N>::CT, min_blocks<float, Shape<N>::E>(Shape<N>::CT))
     k_bin_x_pipe(const float2* G, int64_t spec_stride, int ell, int h0, int M, const float2* __restrict__ F0,
@@ -590,76 +639,76 @@ __global__ void __launch_bounds__(Shape<N>::CT, min_blocks<float, Shape<N>::E>(S
   wb.w = reinterpret_cast<float*>(wb.b + ba.nk);
   wb.init();
   const int c = threadIdx.x % TW, t = threadIdx.x / TW;
-  constexpr int ntz = NH / TW;
-  constexpr int64_t si = (int64_t)N * NH;
-  const float* yl = ytab;  // slot of harmonic h0; the group's slots follow
+  constexpr int64_t si = Lay<N>::XI, modes = (int64_t)N * N * NH;
+  // stage k of the block's tile q into half `buf`: k < M harmonic h0 + k, k = M the F0 tile
+  auto issue = [&](int q, int k, int buf) {
+    const int tile = ba.xtiles[q];
+    const int kt = tile / N, j = tile - kt * N;  // x tiles in storage order
+    const C* Gs = (k < M ? G + (int64_t)k * spec_stride : F0) + Lay<N>::at(0, j, kt * TW);
+    C* dG = sG + buf * N * TW;
+    for (int u = threadIdx.x; u < N * GCH; u += CT) {
+      const int i = u / GCH, part = u - i * GCH;
+      cp_async16(dG + i * TW + part * 2, Gs + i * si + part * 2);
+    }
+    if (k < M) {
+      // the table block of a tile is contiguous, in the tile's own [i][c] order
+      const float* Ys = ytab + (int64_t)k * modes + Lay<N>::table_tile(kt, j);
+      float* dY = sY + buf * N * TW;
+      for (int u = threadIdx.x; u < N * YCH; u += CT) cp_async16(dY + u * 4, Ys + u * 4);
+    }
+    cp_async_commit();
+  };
   __syncthreads();
+  int buf = 0;
+  if ((int)blockIdx.x < ba.n_xtiles) issue(blockIdx.x, 0, 0);
   for (int q = blockIdx.x; q < ba.n_xtiles; q += gridDim.x) {
     const int tile = ba.xtiles[q];
-    const int j = tile / ntz, kz0 = (tile - j * ntz) * TW;
-    const int kz = kz0 + c;
-    const int64_t off0 = (int64_t)j * NH + kz0, off = off0 + c;
-    auto issue = [&](int s, int buf) {
-      const C* Gs = G + (int64_t)s * spec_stride + off0;
-      C* dG = sG + buf * N * TW;
-      for (int q = threadIdx.x; q < N * GCH; q += CT) {
-        const int i = q / GCH, part = q - i * GCH;
-        cp_async16(dG + i * TW + part * 2, Gs + i * si + part * 2);
-      }
-      const float* Ys = yl + (int64_t)s * (si * N) + off0;
-      float* dY = sY + buf * N * TW;
-      for (int q = threadIdx.x; q < N * YCH; q += CT) {
-        const int i = q / YCH, part = q - i * YCH;
-        cp_async16(dY + i * TW + part * 4, Ys + i * si + part * 4);
-      }
-      cp_async_commit();
-    };
-    issue(0, 0);
-    C f0[E];
-    float acc[E];
+    const int kt = tile / N, j = tile - kt * N;
+    const int kz = kt * TW + c;
+    C sum[E];
 #pragma unroll
-    for (int e = 0; e < E; e++) {
-      f0[e] = f0_for(F0[off + (t + Tc * e) * si], ba.odd);
-      acc[e] = 0.f;
-    }
-    for (int s = 0; s < M; s++) {
-      const int buf = s & 1;
-      if (s + 1 < M) {
-        issue(s + 1, buf ^ 1);  // the other half was last read before the previous transform's final barrier
+    for (int e = 0; e < E; e++) sum[e] = mk(0.f, 0.f);
+    for (int k = 0; k <= M; k++, buf ^= 1) {
+      const int nq = k < M ? q : q + (int)gridDim.x, nk = k < M ? k + 1 : 0;
+      if (nq < ba.n_xtiles) {
+        // that half was last read before a barrier every thread has passed: the end of a
+        // transform, or the fold after an F0 stage
+        issue(nq, nk, buf ^ 1);
         cp_async_wait<1>();
       } else {
         cp_async_wait<0>();
       }
-      __syncthreads();  // harmonic s landed for the whole block
+      __syncthreads();  // stage k landed for the whole block
       C* tg = sG + buf * N * TW;
-      const float* ty = sY + buf * N * TW;
-      C v[E];
-      float yv[E];
+      if (k < M) {
+        const float* ty = sY + buf * N * TW;
+        C v[E];
+        float yv[E];
 #pragma unroll
-      for (int e = 0; e < E; e++) {
-        v[e] = tg[(t + Tc * e) * TW + c];
-        yv[e] = ty[(t + Tc * e) * TW + c];
-      }
-      __syncthreads();  // the tile becomes the transform's exchange buffer
-      fft_any<XP, C, E, N, kInterleaved, TW, -1>(v, tg, t, c, twf);
+        for (int e = 0; e < E; e++) {
+          v[e] = tg[(t + Tc * e) * TW + c];
+          yv[e] = ty[(t + Tc * e) * TW + c];
+        }
+        __syncthreads();  // the tile becomes the transform's exchange buffer
+        fft_any<XP, C, E, N, kInterleaved, TW, -1>(v, tg, t, c, twf);
 #pragma unroll
-      for (int e = 0; e < E; e++) acc[e] += yv[e] * (v[e].x * f0[e].x + v[e].y * f0[e].y);  // Y(k=0) = 0
-    }
-    if (j != N / 2) {
-      const float mult = kz ? 2.f : 1.f;
-      const int ny = sfreq<N>(j);
+        for (int e = 0; e < E; e++) sum[e] = mk(fmaf(yv[e], v[e].x, sum[e].x), fmaf(yv[e], v[e].y, sum[e].y));
+      } else if (j != N / 2) {
+        const float mult = kz ? 2.f : 1.f;
+        const int ny = sfreq<N>(j);
 #pragma unroll
-      for (int e = 0; e < E; e++) {
-        const int ii = t + Tc * e;
-        if (ii == N / 2) continue;
-        const int nx = sfreq<N>(ii);
-        const int n2 = nx * nx + ny * ny + kz * kz;
-        const int b = ba.bin_of_n2[n2];
-        if (b >= 0 && n2 > 0) {
-          auto a = acc[e];
-          using V = decltype(a);
-          if (ba.permode_w) a = per_mode_w2<V, N>(a, static_cast<const cx<V>*>(ba.permode_w), ii, j, kz);
-          wb.add(b, mult * a);
+        for (int e = 0; e < E; e++) {
+          const int ii = t + Tc * e;
+          if (ii == N / 2) continue;
+          const int nx = sfreq<N>(ii);
+          const int n2 = nx * nx + ny * ny + kz * kz;
+          const int b = ba.bin_of_n2[n2];
+          if (b >= 0 && n2 > 0) {  // Y(k = 0) = 0
+            const C f = f0_for(tg[ii * TW + c], ba.odd);
+            float a = sum[e].x * f.x + sum[e].y * f.y;
+            if (ba.permode_w) a = per_mode_w2<float, N>(a, static_cast<const cx<float>*>(ba.permode_w), ii, j, kz);
+            wb.add(b, mult * a);
+          }
         }
       }
     }

@@ -145,13 +145,14 @@ __host__ __device__ constexpr int ylm_min_blocks(int lt, bool xp = false) {
 // Twiddle and phase tables hold ux<T> entries (FP32: {cos, sin, 1/|w| - 1, 0}); the
 // compensation table holds cx<T> {1/W_d rounded, its relative rounding error}.
 // Y_lm(khat) table of the FP32 binning pass: harmonic slots of l = 2, 4, ..., l_max in order,
-// 2l+1 each (h order of the harmonics), every slot one value per stored mode [i][j][kz].
+// 2l+1 each (h order of the harmonics), every slot one value per stored mode, one contiguous
+// block of N x tw values per x tile (j, kz tile) of the binning pass, rows i.
 __host__ __device__ constexpr int ytab_base(int ell) {
   int b = 0;
   for (int l = 2; l < ell; l += 2) b += 2 * l + 1;
   return b;
 }
-void launch_ytab_build(float* ytab, int N, int ell_max, int nsm, cudaStream_t s);
+void launch_ytab_build(float* ytab, int N, int tw, int ell_max, int nsm, cudaStream_t s);
 // Y_lm(rhat) of every mesh node for the Y-weighted z pass (FP32 contexts): the same harmonic
 // slots as the Y_lm(khat) table, every slot one value per node [i][j][k], built in FP64 and
 // rounded once. Evaluated in FP32 per node instead, the weights carry errors that are coherent
@@ -162,7 +163,7 @@ struct RGeo {
 };
 void launch_rtab_build(float* rtab, int N, int ell_max, const RGeo& g, int nsm, cudaStream_t s);
 // Cartesian k-space factors mult_q khat^q of every stored mode, q = 0..20 (kCartItems slots).
-void launch_ctab_build(float* ctab, int N, int nsm, cudaStream_t s);
+void launch_ctab_build(float* ctab, int N, int tw, int nsm, cudaStream_t s);
 
 // Launchers with an `xp` argument run the exact-add FP32 variant of their kernel (xp_engine.cuh)
 // when it is nonzero and T is float; FP64 ignores it.

@@ -370,7 +370,7 @@ pspec_status upload_tables(Ctx* c) {
   if (e != cudaSuccess) return cuda_fail(c, e, "table upload");
   TRY(run(c, PSPEC_K_OTHER, 0.0, [&] { launch_mode_counts(pl.g, c->at<uint32_t>(pl.o_cnt), c->nsm, c->stream); }));
   if (pl.has_ytab)
-    TRY(run(c, PSPEC_K_OTHER, 0.0, [&] { launch_ytab_build(c->at<float>(pl.o_ytab), N, c->p.ell_max, c->nsm, c->stream); }));
+    TRY(run(c, PSPEC_K_OTHER, 0.0, [&] { launch_ytab_build(c->at<float>(pl.o_ytab), N, pl.tf->tw, c->p.ell_max, c->nsm, c->stream); }));
   if (pl.has_rtab) {
     RGeo g;
     for (int d = 0; d < 3; d++) {
@@ -381,7 +381,7 @@ pspec_status upload_tables(Ctx* c) {
     TRY(run(c, PSPEC_K_OTHER, 0.0, [&] { launch_rtab_build(c->at<float>(pl.o_rtab), N, c->p.ell_max, g, c->nsm, c->stream); }));
   }
   if (pl.has_ctab)
-    TRY(run(c, PSPEC_K_OTHER, 0.0, [&] { launch_ctab_build(c->at<float>(pl.o_ctab), N, c->nsm, c->stream); }));
+    TRY(run(c, PSPEC_K_OTHER, 0.0, [&] { launch_ctab_build(c->at<float>(pl.o_ctab), N, pl.tf->tw, c->nsm, c->stream); }));
   e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "table upload");
   return PSPEC_OK;
@@ -422,13 +422,14 @@ pspec_status upload_bins(Ctx* c, const double* edges, int nk) {
     int64_t yr = 0, yw = 0;
     std::vector<int32_t> xt;
     xt.reserve((size_t)N * ntz);
-    for (int j = 0; j < N; j++) {
-      const int64_t ny2 = (int64_t)(j < NH ? j : j - N) * (j < NH ? j : j - N);
-      for (int kz = 0; kz < NH; kz++) {
-        yw += ny2 + (int64_t)kz * kz < n2_cut;
-        if (kz % tw == 0 && ny2 + (int64_t)kz * kz < n2_cut) xt.push_back(j * ntz + kz / tw);
+    // x tiles in storage order, tile = kz tile * N + j; active when the (ky, kz) column's
+    // smallest |n|^2 is below the last bin
+    for (int kt = 0; kt < ntz; kt++)
+      for (int j = 0; j < N; j++) {
+        const int64_t ny2 = (int64_t)(j < NH ? j : j - N) * (j < NH ? j : j - N);
+        if (ny2 + (int64_t)kt * tw * kt * tw < n2_cut) xt.push_back(kt * N + j);
+        for (int kz = kt * tw; kz < (kt + 1) * tw; kz++) yw += ny2 + (int64_t)kz * kz < n2_cut;
       }
-    }
     for (int kz0 = 0; kz0 < NH; kz0 += tw) yr += (int64_t)kz0 * kz0 < n2_cut;
     c->frac_yw = (double)yw / ((double)N * NH);
     c->frac_tile = (double)xt.size() / ((double)N * ntz);
