@@ -13,6 +13,41 @@ constexpr int kSumThreads = 256;
 // non-finite ones): beyond it the periodic reduction of the grid coordinate loses meaning.
 constexpr double kMaxCells = 274877906944.0;  // 2^38
 
+// Grid coordinate of a position along one axis in units of 2^-24 cell, t = (x - corner) N/L 2^24,
+// as one FMA with K = 2^24 N/L and the offset corner K. A particle is valid when every |t| is
+// below 2^62 (|u| < kMaxCells cells; NaN and infinities fail), tested on the exponent bits. The
+// tests and conversions below use integer instructions: GB300's FP64 pipe is narrow, and FP64
+// compares and conversions between FP64 or FP32 and 64-bit integers all run on it.
+struct GridMap {
+  double K, cK[3];
+  __device__ __forceinline__ explicit GridMap(const PaintArgs& a) : K(a.inv_cell * 16777216.0) {
+    cK[0] = a.corner[0] * K;
+    cK[1] = a.corner[1] * K;
+    cK[2] = a.corner[2] * K;
+  }
+  __device__ __forceinline__ double t(double x, int d) const { return fma(x, K, -cK[d]); }
+};
+__device__ __forceinline__ bool grid_ok(double t) {
+  return (int)((__double_as_longlong(t) >> 52) & 0x7ff) < 1023 + 62;
+}
+// round to nearest, ties to even, of a finite double with |t| < 2^62
+__device__ __forceinline__ long long d2ll_rn_int(double t) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(t);
+  const int e = (int)((b >> 52) & 0x7ff);
+  const unsigned long long m = (b & 0xfffffffffffffull) | 0x10000000000000ull;  // 53 bits
+  long long q;
+  if (e >= 1075) {
+    q = (long long)(m << (e - 1075));  // integral; shift <= 9
+  } else if (e < 1022) {
+    q = 0;  // |t| < 1/2
+  } else {
+    const int sh = 1075 - e;  // 1..53
+    const unsigned long long r = m >> sh, rem = m & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    q = (long long)(r + (unsigned long long)((rem > half) | ((rem == half) & (r & 1ull))));
+  }
+  return (b >> 63) ? -q : q;
+}
+
 __device__ __forceinline__ void load_pos(const PaintArgs& a, int64_t p, double& x, double& y, double& z) {
   if (a.pos_f32) {
     const float* q = static_cast<const float*>(a.pos) + 3 * p;
@@ -97,6 +132,7 @@ __device__ __forceinline__ PaintArgs resolve(const PaintArgs& in) {
 __global__ void __launch_bounds__(kSumThreads) k_catalog_partials(PaintArgs a_in, double* out) {
   __shared__ double red[kSumThreads / 32];
   const PaintArgs a = resolve(a_in);
+  const GridMap gm(a);
   double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.count;
        p += (int64_t)gridDim.x * blockDim.x) {
@@ -104,9 +140,7 @@ __global__ void __launch_bounds__(kSumThreads) k_catalog_partials(PaintArgs a_in
     load_pos(a, p, x, y, z);
     const double wc = a.weight ? a.weight[p] : 1.0;
     const double nb = a.nbar ? a.nbar[p] : a.nbar_default;
-    const double ux = (x - a.corner[0]) * a.inv_cell, uy = (y - a.corner[1]) * a.inv_cell,
-                 uz = (z - a.corner[2]) * a.inv_cell;
-    if (!(fabs(ux) < kMaxCells && fabs(uy) < kMaxCells && fabs(uz) < kMaxCells && isfinite(wc) && isfinite(nb)))
+    if (!(grid_ok(gm.t(x, 0)) && grid_ok(gm.t(y, 1)) && grid_ok(gm.t(z, 2)) && isfinite(wc) && isfinite(nb)))
       continue;
     const double wf = fkp_w(a, nb);
     const double v = wc * wf;
@@ -298,7 +332,8 @@ __global__ void __launch_bounds__(256) k_paint(PaintArgs a_in, int is_randoms, d
   const bool uniform = (a.weight == nullptr) && (a.nbar == nullptr);
   const double v_uniform = sign * a.wf_default;
   const Dither d_uniform = dither_of(v_uniform);
-  const double lim = (double)N;
+  const GridMap gm(a);
+  const int64_t lim24 = (int64_t)N << 24;
   unsigned bad = 0, out = 0;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.count;
        p += (int64_t)gridDim.x * blockDim.x) {
@@ -309,13 +344,11 @@ __global__ void __launch_bounds__(256) k_paint(PaintArgs a_in, int is_randoms, d
       wc = a.weight ? a.weight[p] : 1.0;
       nb = a.nbar ? a.nbar[p] : a.nbar_default;
     }
-    const double ux = (x - a.corner[0]) * a.inv_cell, uy = (y - a.corner[1]) * a.inv_cell,
-                 uz = (z - a.corner[2]) * a.inv_cell;
-    if (!(fabs(ux) < kMaxCells && fabs(uy) < kMaxCells && fabs(uz) < kMaxCells && isfinite(wc) && isfinite(nb))) {
+    const double tx = gm.t(x, 0), ty = gm.t(y, 1), tz = gm.t(z, 2);
+    if (!(grid_ok(tx) && grid_ok(ty) && grid_ok(tz) && (uniform || (isfinite(wc) && isfinite(nb))))) {
       bad++;
       continue;
     }
-    if (ux < 0.0 || ux >= lim || uy < 0.0 || uy >= lim || uz < 0.0 || uz >= lim) out++;
     T v;
     if constexpr (sizeof(T) == 4)
       v = dither_pick(uniform ? d_uniform : dither_of(sign * wc * fkp_w(a, nb)), p, is_randoms);
@@ -324,8 +357,8 @@ __global__ void __launch_bounds__(256) k_paint(PaintArgs a_in, int is_randoms, d
     int ix[3], iy[3], iz[3];
     T wx[3], wy[3], wz[3];
     if constexpr (sizeof(T) == 4) {
-      const int64_t Ux = __double2ll_rn(ux * 16777216.0), Uy = __double2ll_rn(uy * 16777216.0),
-                    Uz = __double2ll_rn(uz * 16777216.0);
+      const int64_t Ux = d2ll_rn_int(tx), Uy = d2ll_rn_int(ty), Uz = d2ll_rn_int(tz);
+      if (Ux < 0 || Ux >= lim24 || Uy < 0 || Uy >= lim24 || Uz < 0 || Uz >= lim24) out++;
       Axis<float, WIN>::nodes(Ux, N, ix, wx);
       Axis<float, WIN>::nodes(Uy, N, iy, wy);
       Axis<float, WIN>::nodes(Uz, N, iz, wz);
@@ -338,6 +371,10 @@ __global__ void __launch_bounds__(256) k_paint(PaintArgs a_in, int is_randoms, d
         scatter<T, WIN>(m2, N, ix, iy, iz, wx, wy, wz, v);
       }
     } else {
+      const double ux = tx * 5.9604644775390625e-8, uy = ty * 5.9604644775390625e-8,
+                   uz = tz * 5.9604644775390625e-8;  // 2^-24: exact
+      const double lim = (double)N;
+      if (ux < 0.0 || ux >= lim || uy < 0.0 || uy >= lim || uz < 0.0 || uz >= lim) out++;
       Axis<double, WIN>::nodes(ux, N, ix, wx);
       Axis<double, WIN>::nodes(uy, N, iy, wy);
       Axis<double, WIN>::nodes(uz, N, iz, wz);
@@ -426,7 +463,8 @@ __global__ void __launch_bounds__(256) k_ptile_prep(PaintArgs a_in, int is_rando
   const bool uniform = (a.weight == nullptr) && (a.nbar == nullptr);
   const double v_uniform = sign * a.wf_default;
   const Dither d_uniform = dither_of(v_uniform);
-  const double lim = (double)N;
+  const GridMap gm(a);
+  const int64_t lim24 = (int64_t)N << 24;
   const int nts = N / kPT;
   unsigned bad = 0, out = 0;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.count;
@@ -438,20 +476,19 @@ __global__ void __launch_bounds__(256) k_ptile_prep(PaintArgs a_in, int is_rando
       wc = a.weight ? a.weight[p] : 1.0;
       nb = a.nbar ? a.nbar[p] : a.nbar_default;
     }
-    const double u[3] = {(x - a.corner[0]) * a.inv_cell, (y - a.corner[1]) * a.inv_cell,
-                         (z - a.corner[2]) * a.inv_cell};
-    if (!(fabs(u[0]) < kMaxCells && fabs(u[1]) < kMaxCells && fabs(u[2]) < kMaxCells && isfinite(wc) &&
-          isfinite(nb))) {
+    const double tt[3] = {gm.t(x, 0), gm.t(y, 1), gm.t(z, 2)};
+    if (!(grid_ok(tt[0]) && grid_ok(tt[1]) && grid_ok(tt[2]) && (uniform || (isfinite(wc) && isfinite(nb))))) {
       bad++;
       ta.tile_of[offset + p] = kNoTile;
       continue;
     }
-    if (u[0] < 0.0 || u[0] >= lim || u[1] < 0.0 || u[1] >= lim || u[2] < 0.0 || u[2] >= lim) out++;
+    const int64_t Ud[3] = {d2ll_rn_int(tt[0]), d2ll_rn_int(tt[1]), d2ll_rn_int(tt[2])};
+    if (Ud[0] < 0 || Ud[0] >= lim24 || Ud[1] < 0 || Ud[1] >= lim24 || Ud[2] < 0 || Ud[2] >= lim24) out++;
     const float v = dither_pick(uniform ? d_uniform : dither_of(sign * wc * fkp_w(a, nb)), p, is_randoms);
     unsigned packed[3];
     int tb[3], span[3];
     for (int d = 0; d < 3; d++) {
-      const int64_t U = __double2ll_rn(u[d] * 16777216.0);
+      const int64_t U = Ud[d];
       int64_t lo, hi;
       footprint<WIN, INTER>(U, lo, hi);
       const int low = wrap(lo, N);  // the footprint's first cell, wrapped; U shifted by the same period
@@ -550,6 +587,46 @@ __device__ __forceinline__ void tile_nodes(int V, int* idx, float* w) {
 
 __device__ __forceinline__ bool in_tile(int i) { return (unsigned)i < (unsigned)kPT; }
 
+// Round to nearest, ties to even, between FP32 and 64-bit integers with integer instructions
+// (the conversion instructions run on the FP64 pipe). f2ll: finite f with |f| < 2^62.
+__device__ __forceinline__ long long f2ll_rn_int(float f) {
+  const unsigned b = __float_as_uint(f);
+  const int e = (int)((b >> 23) & 0xffu);
+  const unsigned m = (b & 0x7fffffu) | 0x800000u;  // 24 bits
+  long long q;
+  if (e >= 150) {
+    q = (long long)((unsigned long long)m << (e - 150));  // integral; shift <= 38
+  } else if (e < 126) {
+    q = 0;  // |f| < 1/2, zero and subnormals included
+  } else {
+    const int sh = 150 - e;  // 1..24
+    const unsigned r = m >> sh, rem = m & ((1u << sh) - 1u), half = 1u << (sh - 1);
+    q = (long long)(r + (unsigned)((rem > half) | ((rem == half) & (r & 1u))));
+  }
+  return (b >> 31) ? -q : q;
+}
+__device__ __forceinline__ float ll2f_rn_int(long long x) {
+  if (x == 0) return 0.f;
+  const unsigned sgn = x < 0 ? 0x80000000u : 0u;
+  const unsigned long long a = x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x;
+  const int nb = 64 - __clzll((long long)a);  // a in [2^(nb-1), 2^nb)
+  unsigned long long r;
+  int e = nb - 1;
+  if (nb <= 24) {
+    r = a << (24 - nb);
+  } else {
+    const int sh = nb - 24;
+    const unsigned long long rem = a & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    r = a >> sh;
+    r += (unsigned long long)((rem > half) | ((rem == half) & (r & 1ull)));
+    if (r == (1ull << 24)) {  // rounded up to the next power of two
+      r >>= 1;
+      e++;
+    }
+  }
+  return __uint_as_float(sgn | ((unsigned)(e + 127) << 23) | ((unsigned)r & 0x7fffffu));
+}
+
 // The contribution v wx wy wz (FP32, rounded as the direct paint rounds it) in units of 2^-S.
 template <int WIN>
 __device__ __forceinline__ void tile_scatter(unsigned long long* acc, const int (&ix)[3], const int (&iy)[3],
@@ -568,7 +645,7 @@ __device__ __forceinline__ void tile_scatter(unsigned long long* acc, const int 
 #pragma unroll
       for (int c = 0; c < K; c++) {
         if (!in_tile(iz[c])) continue;
-        const long long q = __float2ll_rn((vb * wz[c]) * scale);
+        const long long q = f2ll_rn_int((vb * wz[c]) * scale);
         atomicAdd(row + iz[c], (unsigned long long)q);
       }
     }
@@ -616,7 +693,7 @@ __global__ void __launch_bounds__(256) k_ptile_paint(TileArgs ta, float* __restr
     const int mesh = i / kPT3, cell = i - mesh * kPT3;
     const int lx = cell / (kPT * kPT), ly = (cell / kPT) % kPT, lz = cell % kPT;
     const int64_t g = ((int64_t)(tx * kPT + lx) * N + (ty * kPT + ly)) * N + tz * kPT + lz;
-    (mesh ? m2 : m1)[g] = __ll2float_rn((long long)acc[i]) * inv;
+    (mesh ? m2 : m1)[g] = ll2f_rn_int((long long)acc[i]) * inv;
   }
 }
 
