@@ -11,11 +11,11 @@ namespace pspec {
 constexpr int kSumThreads = 256;
 // Positions further than this many cells from the corner are invalid (reported with the
 // non-finite ones): beyond it the periodic reduction of the grid coordinate loses meaning.
-constexpr double kMaxCells = 274877906944.0;  // 2^38
+constexpr int kMaxCellsLog2 = 38;  // |u| < 2^38 cells for a valid particle
 
 // Grid coordinate of a position along one axis in units of 2^-24 cell, t = (x - corner) N/L 2^24,
 // as one FMA with K = 2^24 N/L and the offset corner K. A particle is valid when every |t| is
-// below 2^62 (|u| < kMaxCells cells; NaN and infinities fail), tested on the exponent bits. The
+// below 2^62 (|u| < 2^kMaxCellsLog2 cells; NaN and infinities fail), tested on the exponent bits. The
 // tests and conversions below use integer instructions: GB300's FP64 pipe is narrow, and FP64
 // compares and conversions between FP64 or FP32 and 64-bit integers all run on it.
 struct GridMap {
@@ -28,7 +28,7 @@ struct GridMap {
   __device__ __forceinline__ double t(double x, int d) const { return fma(x, K, -cK[d]); }
 };
 __device__ __forceinline__ bool grid_ok(double t) {
-  return (int)((__double_as_longlong(t) >> 52) & 0x7ff) < 1023 + 62;
+  return (int)((__double_as_longlong(t) >> 52) & 0x7ff) < 1023 + kMaxCellsLog2 + 24;
 }
 // round to nearest, ties to even, of a finite double with |t| < 2^62
 __device__ __forceinline__ long long d2ll_rn_int(double t) {
@@ -627,9 +627,21 @@ __device__ __forceinline__ float ll2f_rn_int(long long x) {
   return __uint_as_float(sgn | ((unsigned)(e + 127) << 23) | ((unsigned)r & 0x7fffffu));
 }
 
+// Adds the 64-bit integer q into the cell's sum held as two 32-bit words (lo at acc[c], hi at
+// acc[c + hi_off]) with 32-bit shared atomics: lo wraps modulo 2^32, and each add that wraps it
+// (the returned old value shows it) carries 1 into hi, so hi:lo is the exact sum modulo 2^64 in
+// any order. The hi add is skipped when it adds 0 (small q, or a small negative q that carried).
+__device__ __forceinline__ void add64(unsigned* acc, int c, int hi_off, long long q) {
+  const unsigned long long u = (unsigned long long)q;
+  const unsigned lo = (unsigned)u, hi = (unsigned)(u >> 32);
+  const unsigned old = atomicAdd(acc + c, lo);
+  const unsigned h = hi + (old + lo < old ? 1u : 0u);
+  if (h) atomicAdd(acc + c + hi_off, h);
+}
+
 // The contribution v wx wy wz (FP32, rounded as the direct paint rounds it) in units of 2^-S.
 template <int WIN>
-__device__ __forceinline__ void tile_scatter(unsigned long long* acc, const int (&ix)[3], const int (&iy)[3],
+__device__ __forceinline__ void tile_scatter(unsigned* acc, int hi_off, const int (&ix)[3], const int (&iy)[3],
                                              const int (&iz)[3], const float (&wx)[3], const float (&wy)[3],
                                              const float (&wz)[3], float v, float scale) {
   constexpr int K = WIN == PSPEC_WINDOW_CIC ? 2 : 3;
@@ -641,30 +653,49 @@ __device__ __forceinline__ void tile_scatter(unsigned long long* acc, const int 
     for (int b = 0; b < K; b++) {
       if (!in_tile(iy[b])) continue;
       const float vb = va * wy[b];
-      unsigned long long* row = acc + (ix[a] * kPT + iy[b]) * kPT;
+      const int row = (ix[a] * kPT + iy[b]) * kPT;
 #pragma unroll
       for (int c = 0; c < K; c++) {
         if (!in_tile(iz[c])) continue;
-        const long long q = f2ll_rn_int((vb * wz[c]) * scale);
-        atomicAdd(row + iz[c], (unsigned long long)q);
+        add64(acc, row + iz[c], hi_off, f2ll_rn_int((vb * wz[c]) * scale));
       }
     }
   }
 }
 
 // One block per tile (every tile, so that empty tiles store their zeros): sums its records into
-// shared 64-bit accumulators, then stores each cell of the tile once.
+// shared 64-bit accumulators (lo words of both meshes, then hi words), then stores each cell of
+// the tile once, four cells along z per 16-byte store. A tile without records stores zeros and
+// skips the accumulators.
 template <int WIN, bool INTER>
 __global__ void __launch_bounds__(256) k_ptile_paint(TileArgs ta, float* __restrict__ m1, float* __restrict__ m2,
                                                      int N, const double* __restrict__ fix) {
-  extern __shared__ unsigned long long acc[];  // [INTER ? 2 : 1][kPT^3]
+  extern __shared__ __align__(16) unsigned acc[];  // lo [NM][kPT^3], then hi [NM][kPT^3]
   constexpr int NM = INTER ? 2 : 1;
+  constexpr int HI = NM * kPT3;
   const int tile = blockIdx.x;
   const unsigned n = ta.cnt[tile];
   const unsigned o = ta.off[tile];
+  const int nts = N / kPT;
+  const int tz = tile % nts, ty = (tile / nts) % nts, tx = tile / (nts * nts);
+  // 16-byte group i of the tile: mesh, then cells (lx, ly, lz..lz+3); its mesh address
+  auto group = [&](int i, int& mesh) {
+    mesh = i / (kPT3 / 4);
+    const int cell = (i - mesh * (kPT3 / 4)) * 4;
+    const int lx = cell / (kPT * kPT), ly = (cell / kPT) % kPT, lz = cell % kPT;
+    return ((int64_t)(tx * kPT + lx) * N + (ty * kPT + ly)) * N + tz * kPT + lz;
+  };
+  if (n == 0) {
+    for (int i = threadIdx.x; i < NM * kPT3 / 4; i += blockDim.x) {
+      int mesh;
+      const int64_t g = group(i, mesh);
+      *reinterpret_cast<float4*>((mesh ? m2 : m1) + g) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    return;  // uniform over the block: no barrier is left behind
+  }
   const double sc = *fix;
   const float scale = (float)sc, inv = (float)(1.0 / sc);  // powers of two: exact
-  for (int i = threadIdx.x; i < NM * kPT3; i += blockDim.x) acc[i] = 0ull;
+  for (int i = threadIdx.x; i < 2 * NM * kPT3 / 4; i += blockDim.x) reinterpret_cast<uint4*>(acc)[i] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
   for (unsigned q = threadIdx.x; q < n; q += blockDim.x) {
     const uint4 r = ta.sorted[o + q];
@@ -677,23 +708,25 @@ __global__ void __launch_bounds__(256) k_ptile_paint(TileArgs ta, float* __restr
     tile_nodes<WIN>(V[0], ix, wx);
     tile_nodes<WIN>(V[1], iy, wy);
     tile_nodes<WIN>(V[2], iz, wz);
-    tile_scatter<WIN>(acc, ix, iy, iz, wx, wy, wz, v, scale);
+    tile_scatter<WIN>(acc, HI, ix, iy, iz, wx, wy, wz, v, scale);
     if (INTER) {
       const int h = 1 << 23;  // half a cell
       tile_nodes<WIN>(V[0] - h, ix, wx);
       tile_nodes<WIN>(V[1] - h, iy, wy);
       tile_nodes<WIN>(V[2] - h, iz, wz);
-      tile_scatter<WIN>(acc + kPT3, ix, iy, iz, wx, wy, wz, v, scale);
+      tile_scatter<WIN>(acc + kPT3, HI, ix, iy, iz, wx, wy, wz, v, scale);
     }
   }
   __syncthreads();
-  const int nts = N / kPT;
-  const int tz = tile % nts, ty = (tile / nts) % nts, tx = tile / (nts * nts);
-  for (int i = threadIdx.x; i < NM * kPT3; i += blockDim.x) {
-    const int mesh = i / kPT3, cell = i - mesh * kPT3;
-    const int lx = cell / (kPT * kPT), ly = (cell / kPT) % kPT, lz = cell % kPT;
-    const int64_t g = ((int64_t)(tx * kPT + lx) * N + (ty * kPT + ly)) * N + tz * kPT + lz;
-    (mesh ? m2 : m1)[g] = ll2f_rn_int((long long)acc[i]) * inv;
+  for (int i = threadIdx.x; i < NM * kPT3 / 4; i += blockDim.x) {
+    int mesh;
+    const int64_t g = group(i, mesh);
+    const uint4 lo = reinterpret_cast<const uint4*>(acc)[i], hi = reinterpret_cast<const uint4*>(acc + HI)[i];
+    auto cell = [&](unsigned l, unsigned h) {
+      return ll2f_rn_int((long long)(((unsigned long long)h << 32) | l)) * inv;
+    };
+    *reinterpret_cast<float4*>((mesh ? m2 : m1) + g) =
+        make_float4(cell(lo.x, hi.x), cell(lo.y, hi.y), cell(lo.z, hi.z), cell(lo.w, hi.w));
   }
 }
 
