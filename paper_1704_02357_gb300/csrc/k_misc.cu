@@ -13,19 +13,22 @@ constexpr int kSumThreads = 256;
 // non-finite ones): beyond it the periodic reduction of the grid coordinate loses meaning.
 constexpr int kMaxCellsLog2 = 38;  // |u| < 2^38 cells for a valid particle
 
-// Grid coordinate of a position along one axis in units of 2^-24 cell, t = (x - corner) N/L 2^24,
-// as one FMA with K = 2^24 N/L and the offset corner K. A particle is valid when every |t| is
-// below 2^62 (|u| < 2^kMaxCellsLog2 cells; NaN and infinities fail), tested on the exponent bits. The
-// tests and conversions below use integer instructions: GB300's FP64 pipe is narrow, and FP64
-// compares and conversions between FP64 or FP32 and 64-bit integers all run on it.
+// Grid coordinate of a position along one axis in units of 2^-24 cell, t = u 2^24 with
+// u = (x - corner) N/L in FP64 (the power-of-two scaling is exact). A particle is valid when every
+// |t| is below 2^62 (|u| < 2^kMaxCellsLog2 cells; NaN and infinities fail), tested on the exponent
+// bits. The tests and conversions below use integer instructions: GB300's FP64 pipe is narrow, and
+// FP64 compares and conversions between FP64 or FP32 and 64-bit integers all run on it. (One FMA,
+// x K - corner K with K = 2^24 N/L, gives the same t but for rare last-bit ties; measured over 30
+// axis-permutation draws of the 512^3 survey catalogs, the FP32 results then came out with higher
+// median errors, so the two-operation form is kept.)
 struct GridMap {
-  double K, cK[3];
-  __device__ __forceinline__ explicit GridMap(const PaintArgs& a) : K(a.inv_cell * 16777216.0) {
-    cK[0] = a.corner[0] * K;
-    cK[1] = a.corner[1] * K;
-    cK[2] = a.corner[2] * K;
+  double c[3], inv;
+  __device__ __forceinline__ explicit GridMap(const PaintArgs& a) : inv(a.inv_cell) {
+    c[0] = a.corner[0];
+    c[1] = a.corner[1];
+    c[2] = a.corner[2];
   }
-  __device__ __forceinline__ double t(double x, int d) const { return fma(x, K, -cK[d]); }
+  __device__ __forceinline__ double t(double x, int d) const { return ((x - c[d]) * inv) * 16777216.0; }
 };
 __device__ __forceinline__ bool grid_ok(double t) {
   return (int)((__double_as_longlong(t) >> 52) & 0x7ff) < 1023 + kMaxCellsLog2 + 24;
@@ -833,8 +836,10 @@ __global__ void k_axpy_randoms(T* __restrict__ m, const T* __restrict__ r, int64
 }
 
 __global__ void k_batch_outputs(const double* __restrict__ P, int n, const double* __restrict__ d,
-                                const int* __restrict__ cur, double* P_all, double* sums_all) {
+                                const int* __restrict__ cur, const BatchOut* __restrict__ bo) {
   const int c = *cur;
+  double* P_all = bo->P_all;
+  double* sums_all = bo->sums_all;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     P_all[(int64_t)c * n + i] = P[i];
   if (blockIdx.x == 0 && threadIdx.x == 0 && sums_all) {
@@ -862,9 +867,9 @@ void launch_axpy_randoms(float* mesh, const float* rmesh, int64_t n, const doubl
 void launch_axpy_randoms(double* mesh, const double* rmesh, int64_t n, const double* derived, cudaStream_t s) {
   k_axpy_randoms<double><<<2048, 256, 0, s>>>(mesh, rmesh, n, derived);
 }
-void launch_batch_outputs(const double* P, int n_ells, int nk, const double* derived, const int* cur, double* P_all,
-                          double* sums_all, cudaStream_t s) {
-  k_batch_outputs<<<(n_ells * nk + 127) / 128, 128, 0, s>>>(P, n_ells * nk, derived, cur, P_all, sums_all);
+void launch_batch_outputs(const double* P, int n_ells, int nk, const double* derived, const int* cur,
+                          const BatchOut* out, cudaStream_t s) {
+  k_batch_outputs<<<(n_ells * nk + 127) / 128, 128, 0, s>>>(P, n_ells * nk, derived, cur, out);
 }
 void launch_advance(int* cur, cudaStream_t s) { k_advance<<<1, 32, 0, s>>>(cur); }
 

@@ -74,8 +74,14 @@ void launch_catalog_final_cached(const double* part_d, int nb_d, const double* r
 void launch_randoms_sums(const double* part_r, int nb_r, double* rsums, cudaStream_t s);
 void launch_axpy_randoms(float* mesh, const float* rmesh, int64_t n, const double* derived, cudaStream_t s);
 void launch_axpy_randoms(double* mesh, const double* rmesh, int64_t n, const double* derived, cudaStream_t s);
-void launch_batch_outputs(const double* P, int n_ells, int nk, const double* derived, const int* cur, double* P_all,
-                          double* sums_all, cudaStream_t s);
+// Destinations of a batch's per-mock results, read by the kernel from device memory (they are
+// uploaded before every batch), so that a captured graph replays into the current call's buffers.
+struct BatchOut {
+  double* P_all;
+  double* sums_all;
+};
+void launch_batch_outputs(const double* P, int n_ells, int nk, const double* derived, const int* cur,
+                          const BatchOut* out, cudaStream_t s);
 void launch_advance(int* cur, cudaStream_t s);
 
 // a2: scatter-add painting; counts invalid and out-of-box particles into derived.

@@ -63,7 +63,7 @@ struct Plan {
   int64_t max_particles;  // capacity of the tile-binned paint (0: direct painting only)
   int ntiles;
   bool cache_randoms;
-  size_t o_rmesh1, o_rmesh2, o_rsums, o_desc, o_cur;
+  size_t o_rmesh1, o_rmesh2, o_rsums, o_desc, o_cur, o_bout;
 };
 
 pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl, std::string* why) {
@@ -195,6 +195,7 @@ pspec_status build_plan(const pspec_params* p, int max_kbins, int nsm, Plan* pl,
     pl->o_rsums = take(4 * sizeof(double));
     pl->o_desc = take((size_t)PSPEC_MAX_BATCH * sizeof(DevCat));
     pl->o_cur = take(sizeof(int));
+    pl->o_bout = take(sizeof(BatchOut));
   }
   pl->total = o;
   return PSPEC_OK;
@@ -227,6 +228,7 @@ struct Ctx {
   int graph_binned = -1;
   int64_t graph_kernels = 0;
   std::vector<DevCat> desc_host;
+  BatchOut bout_host{};  // this batch's output buffers, uploaded to o_bout
   pspec_catalog batch_proto{};  // dtype of the mocks' positions (pointers come from the table)
   pspec_tuning tune{1, 64, 0, 0};
   std::string err;
@@ -796,8 +798,7 @@ pspec_status do_set_randoms(Ctx* c, const pspec_catalog* r) {
 
 // One mock of a batch: sums, paint, mesh -= alpha * randoms, multipoles, outputs, counter.
 template <typename T>
-pspec_status enqueue_mock(Ctx* c, bool binned, int64_t max_count, const int32_t* ells, int n_ells, int nk,
-                          double* P_all, double* sums_all) {
+pspec_status enqueue_mock(Ctx* c, bool binned, int64_t max_count, const int32_t* ells, int n_ells, int nk) {
   const Plan& pl = c->pl;
   PaintArgs a = paint_args(c, &c->batch_proto);
   a.dc = c->at<DevCat>(pl.o_desc);
@@ -818,7 +819,7 @@ pspec_status enqueue_mock(Ctx* c, bool binned, int64_t max_count, const int32_t*
   double* out = c->at<double>(pl.o_out);
   TRY(do_multipoles<T>(c, ells, n_ells, nk, out + 2 * (size_t)nk, out, out + nk));
   TRY(run(c, PSPEC_K_OTHER, 0.0, [&] {
-    launch_batch_outputs(out + 2 * (size_t)nk, n_ells, nk, der, a.cur, P_all, sums_all, c->stream);
+    launch_batch_outputs(out + 2 * (size_t)nk, n_ells, nk, der, a.cur, c->at<BatchOut>(pl.o_bout), c->stream);
   }));
   TRY(run(c, PSPEC_K_OTHER, 0.0, [&] { launch_advance(c->at<int>(pl.o_cur), c->stream); }));
   return PSPEC_OK;
@@ -1093,12 +1094,17 @@ pspec_status pspec_run_batch(void* ctx, const pspec_catalog* mocks, int32_t n_mo
   e = cudaMemcpyAsync(c->at<DevCat>(pl.o_desc), c->desc_host.data(), n_mocks * sizeof(DevCat), cudaMemcpyHostToDevice,
                       c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->at<int>(pl.o_cur), 0, sizeof(int), c->stream);
+  // the destinations go through device memory: a graph captured in an earlier call replays into
+  // this call's buffers
+  c->bout_host = BatchOut{P_all, sums_all};
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->at<BatchOut>(pl.o_bout), &c->bout_host, sizeof(BatchOut), cudaMemcpyHostToDevice, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "batch table upload");
   const bool binned = c->tune.paint_binned && pl.max_particles >= max_count && c->p.precision != PSPEC_FP64;
   const bool f64 = c->p.precision == PSPEC_FP64;
   auto one = [&]() {
-    return f64 ? enqueue_mock<double>(c, binned, max_count, ells, n_ells, n_kbins, P_all, sums_all)
-               : enqueue_mock<float>(c, binned, max_count, ells, n_ells, n_kbins, P_all, sums_all);
+    return f64 ? enqueue_mock<double>(c, binned, max_count, ells, n_ells, n_kbins)
+               : enqueue_mock<float>(c, binned, max_count, ells, n_ells, n_kbins);
   };
   if (!use_graph) {
     for (int i = 0; i < n_mocks; i++) TRY(one());
