@@ -45,7 +45,9 @@ def test_survey_shaped_high_ell_fp32():
     assert rep[2]["bins_checked"] > 0 and rep[4]["bins_checked"] > 0
 
 
-def test_survey_512_l4_matches_oracle():
+@pytest.fixture(scope="module")
+def survey512_l4():
+    """The benchmark's 512^3 catalog and the oracle's multipoles of it (computed once here)."""
     geo = synth.survey_geometry(box_size=2000.0)
     fld = synth.lognormal_field(256, geo.box_size, geo.box_corner, seed=3)
     d = synth.survey_catalog(fld, geo, nbar=3e-4, seed=33)
@@ -56,15 +58,22 @@ def test_survey_512_l4_matches_oracle():
     kn = math.pi * 512 / 2000.0
     edges = 0.005 * np.arange(int(kn / 0.005) + 1)
     ells = [0, 2, 4]
-    g = run_gpu(p, d, r, ells, edges, precision="fp32", max_particles=d.size + r.size)
-    o = E.multipoles(d, r, p, ells, edges)
+    return d, r, p, edges, ells, E.multipoles(d, r, p, ells, edges)
+
+
+# fp32: the library default (exact-add harmonic and inverse transforms); fp32_plain: plain FP32
+# radix trees, the transforms the benchmark's headline runs
+@pytest.mark.parametrize("precision", ["fp32", "fp32_plain"])
+def test_survey_512_l4_matches_oracle(survey512_l4, precision):
+    d, r, p, edges, ells, o = survey512_l4
+    g = run_gpu(p, d, r, ells, edges, precision=precision, max_particles=d.size + r.size)
     np.testing.assert_array_equal(g["n_modes"], o["n_modes"])
     np.testing.assert_allclose(g["k_mean"], o["k_mean"], rtol=1e-6)
     assert abs(g["stats"]["alpha"] - o["alpha"]) <= 1e-14 * o["alpha"]
     rep = {}
     check_fp32(g, o, ells, report=rep)
     assert rep[0]["bins_checked"] == len(edges) - 1 and rep[2]["bins_checked"] > 20 and rep[4]["bins_checked"] > 0
-    print("full-size parity:", rep)
+    print("full-size parity", precision, rep)
 
 
 def test_survey_512_tsc_l16_matches_golden():
@@ -93,7 +102,8 @@ def test_survey_512_tsc_l16_matches_golden():
     print("full-size l <= 16 parity:", {ell: (v["bins_checked"], f'{v["max_rel"]:.2e}') for ell, v in rep.items()})
 
 
-def test_survey_512_l4_second_draw_matches_golden():
+@pytest.mark.parametrize("precision", ["fp32", "fp32_plain"])
+def test_survey_512_l4_second_draw_matches_golden(precision):
     """A second Poisson draw of the 512^3 survey catalog (data seed 34), against the FP64
     oracle's values stored by tests/golden/make_survey512_cic_l4_s34.py. One of its high-k bins
     has P_4 = 1.4% of P_0, so any error that does not average down over the k shell (an FP32
@@ -109,7 +119,7 @@ def test_survey_512_l4_second_draw_matches_golden():
     assert d.size == int(gold["n_data"]) and r.size == int(gold["n_randoms"])
     np.testing.assert_array_equal(edges, gold["edges"])
     ells = [int(x) for x in gold["ells"]]
-    g = run_gpu(p, d, r, ells, edges, precision="fp32", max_particles=d.size + r.size)
+    g = run_gpu(p, d, r, ells, edges, precision=precision, max_particles=d.size + r.size)
     np.testing.assert_array_equal(g["n_modes"], gold["n_modes"])
     assert abs(g["stats"]["alpha"] - float(gold["alpha"])) <= 1e-14 * float(gold["alpha"])
     rep = {}
