@@ -195,9 +195,10 @@ __global__ void __launch_bounds__(ZShape<N, XP>::ZT, min_blocks<T, ZShape<N, XP>
 // For `rows` rows of f and the M harmonics h0..h0+M-1 of multipole l. Every point sweeps
 // its harmonics once ((x+iy)^a carried from one |m| to the next) into a shared staging
 // area of nseq = M*rows real rows; then each of the nseq*Tz threads loads its slots, the
-// sequences are transformed (each sequence's staging row is its exchange row) and unpacked
-// into the M spectra. With the Y_lm(rhat) table and sequences within one warp, each warp
-// stages its own sequences, and the pass runs without block barriers.
+// sequences are transformed (the staging area is reused as the exchange buffer) and unpacked
+// into the M spectra. With the Y_lm(rhat) table and sequences within one warp, each thread loads
+// its own slots of f and of the table and multiplies them in registers: no staging, and no block
+// barrier.
 template <typename T, int N, int LT, bool XP>
 __global__ void __launch_bounds__(ylm_thread_cap(LT), sizeof(T) == 4 ? ylm_min_blocks(LT, XP) : 0) k_ylm_r2c_z(const T* __restrict__ f, cx<T>* __restrict__ out,
                                                   int64_t spec_stride, int ell, int h0, int M,
@@ -209,30 +210,27 @@ __global__ void __launch_bounds__(ylm_thread_cap(LT), sizeof(T) == 4 ? ylm_min_b
   using S = ZShape<N, XP>;
   constexpr int L = N / 2, E = S::E, Tc = S::Tz;
   extern __shared__ __align__(16) unsigned char smraw[];
-  // staging stride in reals: N, or (warp-local staging) one exchange row, so that a sequence's
-  // staging row is its own exchange row
-  constexpr int SP = 2 * padded_len(L);
-  T* stage = reinterpret_cast<T*>(smraw);  // [nseq][N or SP] reals, then the exchange buffer
+  T* stage = reinterpret_cast<T*>(smraw);  // [nseq][N] reals, then the exchange buffer
   C* xb = reinterpret_cast<C*>(smraw);
   const int row0 = blockIdx.x * rows;
   const int a_lo = LT < 0 ? 0 : harm_a(h0), a_hi = LT < 0 ? 0 : harm_a(h0 + M - 1);
   const int sq = threadIdx.x / Tc, t = threadIdx.x - sq * Tc;
-  constexpr bool kWarpTable = sizeof(T) == 4 && LT >= 0 && S::ZW && SP % 4 == 0;  // 16-byte rows
+  C v[E];
+  constexpr bool kWarpTable = sizeof(T) == 4 && LT >= 0 && S::ZW;
   const bool warp_local = kWarpTable && rtab != nullptr;  // uniform over the block
   if constexpr (kWarpTable) {
     if (rtab) {
-      // the Tc threads of sequence (s, r) stage f * Y_lm(rhat) of their own row, 4 nodes a step
+      // the Tc threads of sequence (s, r) load their own slots: complex slot k of the row packs
+      // f Y_lm(rhat) of nodes 2k and 2k + 1
       constexpr int64_t pts = (int64_t)N * N * N;
-      constexpr int NV = N / 4;
       const int s = sq / rows, r = sq - s * rows;
       const int64_t at0 = (int64_t)(row0 + r) * N;
-      const float4* fr = reinterpret_cast<const float4*>(f + at0);
-      const float4* yr = reinterpret_cast<const float4*>(rtab + (int64_t)s * pts + at0);
-      float4* dr = reinterpret_cast<float4*>(stage + sq * SP);
-#pragma unroll 4
-      for (int kv = t; kv < NV; kv += Tc) {
-        const float4 fv = __ldg(fr + kv), y = __ldg(yr + kv);
-        dr[kv] = make_float4(fv.x * y.x, fv.y * y.y, fv.z * y.z, fv.w * y.w);
+      const float2* fr = reinterpret_cast<const float2*>(f + at0);
+      const float2* yr = reinterpret_cast<const float2*>(rtab + (int64_t)s * pts + at0);
+#pragma unroll
+      for (int e = 0; e < E; e++) {
+        const float2 a = __ldg(fr + t + Tc * e), b = __ldg(yr + t + Tc * e);
+        v[e] = mk(a.x * b.x, a.y * b.y);
       }
     }
   } else if constexpr (sizeof(T) == 4 && LT >= 0) {
@@ -326,19 +324,13 @@ __global__ void __launch_bounds__(ylm_thread_cap(LT), sizeof(T) == 4 ? ylm_min_b
       }
     }
   }
-  if (warp_local)
-    __syncwarp();
-  else
+  if (!warp_local) {
     __syncthreads();
-  const C* stc = reinterpret_cast<const C*>(stage);
-  C v[E];
+    const C* stc = reinterpret_cast<const C*>(stage);
 #pragma unroll
-  for (int e = 0; e < E; e++) v[e] = stc[sq * (warp_local ? SP / 2 : L) + t + Tc * e];
-  // the staging area becomes the exchange buffer: a sequence's own row (warp-local), else shared
-  if (warp_local)
-    __syncwarp();
-  else
-    __syncthreads();
+    for (int e = 0; e < E; e++) v[e] = stc[sq * L + t + Tc * e];
+    __syncthreads();  // the staging area becomes the exchange buffer
+  }
   fft_any<XP, C, E, L, kPaddedRows, 1, -1, S::ZW>(v, xb, t, sq, twh);
   // mirrors through shared memory (shuffles would raise this kernel's register count, measured slower)
 #pragma unroll
