@@ -166,9 +166,9 @@ def traffic_for(kernel, alg_bytes_per_launch):
     return ent["dram_bytes_per_algorithmic_byte"] * alg_bytes_per_launch
 
 
-# sources that hold no transform pass and set none of their launch shapes (paint, catalog sums,
-# the no-allocation entry point, wedges): a change there leaves the passes' ncu counters valid
-_NOT_PASSES = {"k_misc.cu", "noalloc.cu", "mu_edges.cu"}
+# sources that hold no transform pass and set none of their launch shapes (paint and its integer
+# conversions, catalog sums, the no-allocation entry point, wedges): a change there leaves the passes' ncu counters valid
+_NOT_PASSES = {"k_misc.cu", "intconv.cuh", "noalloc.cu", "mu_edges.cu"}
 
 
 def source_hash():

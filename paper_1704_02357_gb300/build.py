@@ -18,7 +18,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpspec.so")
 SOURCES = ["k_fft.cu", "k_misc.cu", "pspec_api.cu", "noalloc.cu", "mu_edges.cu", "pass_small.cu", "pass_256.cu", "pass_512.cu",
            "pass_1024.cu", "pass_3small.cu", "pass_384.cu", "pass_768.cu"]
-HEADERS = ["common.cuh", "fft_engine.cuh", "xp_engine.cuh", "launch.h", "k_fft_kernels.cuh"]
+HEADERS = ["common.cuh", "fft_engine.cuh", "xp_engine.cuh", "intconv.cuh", "launch.h", "k_fft_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -5,6 +5,7 @@
 //   a7 wedges:       Sec. 2.2 eqs. wedge-est and Lbar.
 #include <cmath>
 #include "launch.h"
+#include "intconv.cuh"
 
 namespace pspec {
 
@@ -16,8 +17,8 @@ constexpr int kMaxCellsLog2 = 38;  // |u| < 2^38 cells for a valid particle
 // Grid coordinate of a position along one axis in units of 2^-24 cell, t = u 2^24 with
 // u = (x - corner) N/L in FP64 (the power-of-two scaling is exact). A particle is valid when every
 // |t| is below 2^62 (|u| < 2^kMaxCellsLog2 cells; NaN and infinities fail), tested on the exponent
-// bits. The tests and conversions below use integer instructions: GB300's FP64 pipe is narrow, and
-// FP64 compares and conversions between FP64 or FP32 and 64-bit integers all run on it. (One FMA,
+// bits. The test and the conversions (intconv.cuh) use integer instructions: GB300's FP64 pipe is
+// narrow, and FP64 compares and conversions between FP64 or FP32 and 64-bit integers all run on it. (One FMA,
 // x K - corner K with K = 2^24 N/L, gives the same t but for rare last-bit ties; measured over 30
 // axis-permutation draws of the 512^3 survey catalogs, the FP32 results then came out with higher
 // median errors, so the two-operation form is kept.)
@@ -30,26 +31,7 @@ struct GridMap {
   }
   __device__ __forceinline__ double t(double x, int d) const { return ((x - c[d]) * inv) * 16777216.0; }
 };
-__device__ __forceinline__ bool grid_ok(double t) {
-  return (int)((__double_as_longlong(t) >> 52) & 0x7ff) < 1023 + kMaxCellsLog2 + 24;
-}
-// round to nearest, ties to even, of a finite double with |t| < 2^62
-__device__ __forceinline__ long long d2ll_rn_int(double t) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(t);
-  const int e = (int)((b >> 52) & 0x7ff);
-  const unsigned long long m = (b & 0xfffffffffffffull) | 0x10000000000000ull;  // 53 bits
-  long long q;
-  if (e >= 1075) {
-    q = (long long)(m << (e - 1075));  // integral; shift <= 9
-  } else if (e < 1022) {
-    q = 0;  // |t| < 1/2
-  } else {
-    const int sh = 1075 - e;  // 1..53
-    const unsigned long long r = m >> sh, rem = m & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
-    q = (long long)(r + (unsigned long long)((rem > half) | ((rem == half) & (r & 1ull))));
-  }
-  return (b >> 63) ? -q : q;
-}
+__device__ __forceinline__ bool grid_ok(double t) { return exp_below(t, kMaxCellsLog2 + 24); }
 
 __device__ __forceinline__ void load_pos(const PaintArgs& a, int64_t p, double& x, double& y, double& z) {
   if (a.pos_f32) {
@@ -589,46 +571,6 @@ __device__ __forceinline__ void tile_nodes(int V, int* idx, float* w) {
 }
 
 __device__ __forceinline__ bool in_tile(int i) { return (unsigned)i < (unsigned)kPT; }
-
-// Round to nearest, ties to even, between FP32 and 64-bit integers with integer instructions
-// (the conversion instructions run on the FP64 pipe). f2ll: finite f with |f| < 2^62.
-__device__ __forceinline__ long long f2ll_rn_int(float f) {
-  const unsigned b = __float_as_uint(f);
-  const int e = (int)((b >> 23) & 0xffu);
-  const unsigned m = (b & 0x7fffffu) | 0x800000u;  // 24 bits
-  long long q;
-  if (e >= 150) {
-    q = (long long)((unsigned long long)m << (e - 150));  // integral; shift <= 38
-  } else if (e < 126) {
-    q = 0;  // |f| < 1/2, zero and subnormals included
-  } else {
-    const int sh = 150 - e;  // 1..24
-    const unsigned r = m >> sh, rem = m & ((1u << sh) - 1u), half = 1u << (sh - 1);
-    q = (long long)(r + (unsigned)((rem > half) | ((rem == half) & (r & 1u))));
-  }
-  return (b >> 31) ? -q : q;
-}
-__device__ __forceinline__ float ll2f_rn_int(long long x) {
-  if (x == 0) return 0.f;
-  const unsigned sgn = x < 0 ? 0x80000000u : 0u;
-  const unsigned long long a = x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x;
-  const int nb = 64 - __clzll((long long)a);  // a in [2^(nb-1), 2^nb)
-  unsigned long long r;
-  int e = nb - 1;
-  if (nb <= 24) {
-    r = a << (24 - nb);
-  } else {
-    const int sh = nb - 24;
-    const unsigned long long rem = a & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
-    r = a >> sh;
-    r += (unsigned long long)((rem > half) | ((rem == half) & (r & 1ull)));
-    if (r == (1ull << 24)) {  // rounded up to the next power of two
-      r >>= 1;
-      e++;
-    }
-  }
-  return __uint_as_float(sgn | ((unsigned)(e + 127) << 23) | ((unsigned)r & 0x7fffffu));
-}
 
 // Adds the 64-bit integer q into the cell's sum held as two 32-bit words (lo at acc[c], hi at
 // acc[c + hi_off]) with 32-bit shared atomics: lo wraps modulo 2^32, and each add that wraps it
