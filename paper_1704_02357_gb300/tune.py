@@ -38,14 +38,23 @@ def save_cache(cache: dict, path: str = DEFAULT_PATH) -> None:
 
 
 def tuned(est, data_pos, randoms_pos, ells, k_edges, path: Optional[str] = DEFAULT_PATH, reps: int = 2,
-          **cat) -> dict:
-    """Apply the cached tuning for this estimator's key, or run the autotuner and cache it."""
+          keep_exact_paint: bool = True, **cat) -> dict:
+    """Apply the cached tuning for this estimator's key, or run the autotuner and cache it.
+
+    With `keep_exact_paint` (the default) a context that holds the tile-paint buffers keeps the
+    exact tile-binned paint even where the search found the direct paint faster: the direct
+    paint adds FP32 atomics in an order that changes from run to run, so it is not the same
+    result at another speed."""
     key = key_for(est)
     cache = load_cache(path) if path else {}
     if key in cache:
         est.set_tuning(**cache[key])
         return dict(cache[key], cached=True)
     best = est.autotune(data_pos, randoms_pos, ells, k_edges, reps=reps, **cat)
+    has_tiles = int(getattr(getattr(est, "params", None), "max_particles", 0) or 0) > 0
+    if keep_exact_paint and has_tiles and best.get("paint_binned") == 0:
+        best = dict(best, paint_binned=1)
+        est.set_tuning(**best)
     if path:
         cache[key] = best
         save_cache(cache, path)

@@ -279,3 +279,29 @@ def test_pooled_correlation_recovers_a_known_correlation():
     assert np.max(np.abs(P - R)) < 0.05
     with pytest.raises(ValueError):
         covariance.pooled_correlation(np.ones((10, 3, 2)))
+
+
+def test_autotune_keeps_the_exact_paint_where_the_context_holds_its_buffers(tmp_path, monkeypatch):
+    import types
+    monkeypatch.setattr(tune, "key_for", lambda est: "key")
+
+    class DirectFaster(FakeTunable):
+        def __init__(self, max_particles):
+            super().__init__()
+            self.params = types.SimpleNamespace(max_particles=max_particles)
+
+        def autotune(self, *a, **kw):
+            self.tuned_calls += 1
+            return {"tile_y": 0, "ylm_harmonics": 8, "bin_blocks_per_sm": 0, "paint_binned": 0}
+
+    est = DirectFaster(10 ** 6)
+    got = tune.tuned(est, None, None, [0, 2, 4], [0.0, 0.1], path=str(tmp_path / "a.json"))
+    assert got["paint_binned"] == 1 and est.applied["paint_binned"] == 1
+    assert tune.load_cache(str(tmp_path / "a.json"))["key"]["paint_binned"] == 1
+    # without tile buffers the direct paint is the only one, and the search's choice stands
+    est0 = DirectFaster(0)
+    assert tune.tuned(est0, None, None, [0, 2, 4], [0.0, 0.1], path=str(tmp_path / "b.json"))["paint_binned"] == 0
+    # the caller may let the search choose the direct paint
+    est1 = DirectFaster(10 ** 6)
+    got1 = tune.tuned(est1, None, None, [0, 2, 4], [0.0, 0.1], path=str(tmp_path / "c.json"), keep_exact_paint=False)
+    assert got1["paint_binned"] == 0
